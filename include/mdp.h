@@ -1,0 +1,270 @@
+/*
+ * mdp.h -- C ABI of the GB300 (sm_103a) MDP path planner library
+ *          (libmdp_gb300.so).
+ *
+ * The library builds and solves the finite-horizon, undiscounted, total-cost
+ * MDP of Chowdhury & Subramani, "Optimal Path Planning of Autonomous Marine
+ * Vehicles in Stochastic Dynamic Ocean Flows using a GPU-Accelerated
+ * Algorithm" (arXiv 2109.00857):
+ *   - model build (Sec. III-A/B/C, Alg. 1 and Alg. 2): for every (time step,
+ *     grid cell, action) it draws N realizations of the dynamically orthogonal
+ *     (DO) velocity v = vbar + mu_i v~_i (Sec. II-C), takes one Euler step
+ *     x' = x + (v + a) dt (Sec. II-A), counts the landing cells on the
+ *     neighbouring sub-grid and emits sparse P(s'|s,a) = count/N and the
+ *     expected one-step reward R(s,a) for the time, energy and net-energy
+ *     objectives (Eqs. Rsa_time, Rsa_energyConsumption, Rsa_NetEnergy, with
+ *     the mean scalar field only, as proved in Sec. III-A);
+ *   - sparse value iteration (Sec. II-B, Sec. III-D):
+ *     v_{k+1}(s) = max_a sum_{s'} P(s'|s,a) [r + v_k(s')], greedy policy.
+ *
+ * Conventions used by every call
+ *   - Pointers named *_h are HOST pointers; every other array pointer is a
+ *     DEVICE pointer on the current CUDA device.  The caller owns every array
+ *     it passes and keeps it alive until the work on `stream` completes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work of a call is ordered on that stream.
+ *   - Kinematics are in grid units: the agent starts at the centre of cell
+ *     (i, j), i.e. x = (i + 1/2) dx, and cell(x) = floor(x / dx) with
+ *     half-open cells.  Velocities are in length per time, dx and dt scale them.
+ *   - State index s = t*Nc + j*Nx + i (Nc = Nx*Ny), |S| = Nt*Nc; the sink
+ *     state (outside the domain, obstacle, beyond the horizon) is s = |S|
+ *     with V(sink) = 0.
+ *   - Exported rows follow the paper's appended layout: row = a*|S| + s
+ *     (Sec. III-C, P appended over actions), successors ascending, sink last.
+ *   - Errors: every call returns an mdp_status; mdp_last_error() gives a
+ *     thread-local message.  The library never traps, asserts on the device,
+ *     exits or aborts; device-side problems are reported through a status
+ *     word read back once per call.  There is no CPU fallback: without a
+ *     usable CUDA device every call returns MDP_ERR_CUDA.
+ */
+#ifndef MDP_GB300_H
+#define MDP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MDP_OK = 0,
+  MDP_ERR_ARG = -1,               /* invalid argument (message says which) */
+  MDP_ERR_OOM = -2,               /* device allocation failed or pool capacity hit */
+  MDP_ERR_SUBGRID_OVERFLOW = -3,  /* a landing fell outside the neighbouring sub-grid */
+  MDP_ERR_ELL_OVERFLOW = -4,      /* a row had more successors than the row cap */
+  MDP_ERR_TIMEOUT = -5,           /* a bounded wait expired */
+  MDP_ERR_CUDA = -6,              /* a CUDA runtime error (message has the CUDA string) */
+  MDP_ERR_BUDGET = -7,            /* request does not fit the server's HBM budget */
+  MDP_ERR_CANCELLED = -8,         /* request cancelled or server shutting down */
+  MDP_ERR_NOT_FOUND = -9,         /* unknown ticket / env id */
+  MDP_ERR_PENDING = -10           /* result not ready within the poll timeout */
+} mdp_status;
+
+/* prob_type (Alg. 1 input): the mission objective. */
+typedef enum { MDP_OBJ_TIME = 0, MDP_OBJ_ENERGY = 1, MDP_OBJ_NET_ENERGY = 2 } mdp_objective;
+
+/* Arithmetic of a build/solve.  FP32 is the production path.  FP64_CHECK runs
+ * the literal FP64 formulas in the oracle's operation order (no contraction)
+ * so that counts are bit-identical to an FP64 reference; it is slow and meant
+ * for small problems. */
+typedef enum { MDP_FP32 = 0, MDP_FP64_CHECK = 1 } mdp_precision;
+
+/* grid_params (Alg. 1 input, Sec. IV): grid sizes, cell side dx, time step dt. */
+typedef struct {
+  int32_t nx, ny, nt;
+  double dx, dt;
+} mdp_grid;
+
+/* prob_params (Alg. 1 input, Sec. II-A): the action space and reward constants.
+ * Action a = f*n_headings + h has heading 2 pi h / n_headings and speed
+ * f_max (f+1)/n_speeds.  If table_h is non-NULL it overrides that rule:
+ * table_h[3a+0..2] = (F cos theta, F sin theta, F) in FP64.  A = n_headings *
+ * n_speeds must be in [1, 32]. */
+typedef struct {
+  int32_t n_headings, n_speeds;
+  double f_max;
+  const double *table_h;  /* host [A][3] or NULL */
+  double c_f;             /* energy function e(F) = c_f F^2 (Eq. Rsa_energyConsumption) */
+  double c_r;             /* scalar-field coefficient (Eq. Rsa_NetEnergy) */
+  double r_term;          /* reward added on reaching a target cell */
+  double r_outbound;      /* reward for obstacle / outside / beyond the horizon */
+} mdp_actions;
+
+/* Environment data (Alg. 1 inputs: vbar, v~_i, mu_i, gbar, m).  Element type of
+ * every floating array is float for MDP_FP32 and double for MDP_FP64_CHECK. */
+typedef struct {
+  int32_t K;               /* number of DO modes, 0..16 */
+  int32_t precision;       /* mdp_precision */
+  const void *vbar;        /* [nt][ny][nx][2] DO mean velocity */
+  const void *modes;       /* [nt][K][ny][nx][2] DO modes */
+  const void *coeffs;      /* [nt][N][K] DO coefficients mu_i(t; w), or NULL: drawn by the
+                              library as sigma_h[k] * z, z ~ N(0,1) from Philox4x64-10 */
+  const double *sigma_h;   /* host [K] coefficient standard deviations (used if coeffs NULL) */
+  uint64_t seed;           /* Philox key word 0 (used if coeffs NULL) */
+  uint64_t mdp_id;         /* Philox key word 1 (used if coeffs NULL) */
+  const void *gbar;        /* [nt][ny][nx] mean scalar field, NULL unless net energy is asked */
+  const uint8_t *obstacle; /* [nt][ny][nx] dynamic obstacle mask m (nonzero = obstacle) */
+  const uint8_t *target;   /* [ny][nx] target (terminal) cells (nonzero = target) */
+} mdp_env;
+
+/* Build options (zero-initialise for defaults). */
+typedef struct {
+  int32_t row_cap;         /* max stored successors per row incl. sink; 0 = 64 */
+  int32_t no_compact;      /* 1: keep the worst-case entry pool instead of compacting it */
+  int32_t threads;         /* build CTA size for FP32 (multiple of 64); 0 = autotuned */
+  int32_t chunk;           /* realizations staged per pass; 0 = autotuned */
+} mdp_build_opts;
+
+typedef struct mdp_model_t *mdp_model;
+
+/* Builds P and R for n_obj objectives from one set of samples (Alg. 1; the
+ * counts do not depend on the objective).  N in [1, 65535], subgrid_L odd in
+ * [1, 255] (0 = smallest window that holds every landing, computed from the
+ * field extremes as the paper sizes it from the component-wise maximum
+ * velocity plus a buffer).  objs_h: host [n_obj], n_obj in [1, 3].
+ * On success *out owns all model memory (free with mdp_model_free).
+ * Returns MDP_ERR_SUBGRID_OVERFLOW if any landing left the sub-grid and
+ * MDP_ERR_ELL_OVERFLOW if a row exceeded row_cap; *out is NULL then.
+ * Synchronises `stream` once at the end to read the status word. */
+mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
+                     int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                     const mdp_build_opts *opts, void *stream, mdp_model *out);
+
+typedef struct {
+  int64_t n_states;        /* |S| = nt*nx*ny (sink excluded) */
+  int32_t A;               /* actions */
+  int32_t N;               /* realizations */
+  int32_t L;               /* sub-grid side used */
+  int32_t n_obj;           /* objectives with an R vector */
+  int32_t objs[3];
+  int32_t precision;
+  int64_t rows;            /* A * |S| */
+  int64_t nnz;             /* stored successors over all rows (sink entries included) */
+  int32_t max_row_nnz;     /* widest row */
+  int64_t pool_columns;    /* 32-entry columns of the sliced-ELL entry pool in use */
+  int64_t device_bytes;    /* device memory owned by the model */
+  int64_t samples;         /* landing evaluations performed (N per sampled (s,a)) */
+  double build_ms;         /* device time of the build kernels (CUDA events) */
+} mdp_model_info_t;
+
+mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *out);
+
+/* Paper-layout CSR export of P and the R of objective slot obj (Sec. III-C COO
+ * rows appended over actions).  rowptr: device int64 [A*|S|+1]; col: device
+ * int64 [nnz] (sink = |S|); count: device int32 [nnz] with P = count/N;
+ * R: device [A*|S|] float (FP32) or double (FP64_CHECK); any of col, count, R
+ * may be NULL to skip it.  Synchronises `stream`. */
+mdp_status mdp_export_csr(mdp_model m, int32_t obj, int64_t *rowptr, int64_t *col,
+                          int32_t *count, void *R, void *stream);
+
+/* Solve schedules. */
+typedef enum {
+  MDP_SOLVE_JACOBI = 0,    /* Gauss-Jacobi sweeps over all states, device residual (Sec. II-B) */
+  MDP_SOLVE_LAYERED = 1    /* one backward pass over time layers t = nt-1..0 (same fixed point) */
+} mdp_solve_method;
+
+typedef struct {
+  int32_t sweeps;          /* sweeps executed (layered: 1) */
+  double residual;         /* max |V_k - V_{k-1}| of the last sweep (layered: 0) */
+  double solve_ms;         /* device time of the solve kernels (CUDA events) */
+  int64_t backups;         /* (s,a) Bellman backups performed */
+} mdp_solve_stats;
+
+/* Value iteration on the model's P and the R of objective slot obj.
+ * V: device [|S|+1] float (FP32) or double (FP64_CHECK), V[|S|] = 0 (sink);
+ * policy: device int16 [|S|], argmax_a with the lowest index winning ties,
+ * -1 for terminal and obstacle start states.  Jacobi starts from V = 0 and
+ * stops when max|V_{k+1} - V_k| <= tol or after max_sweeps sweeps
+ * (0 = nt + 1, which reaches the exact fixed point of this time-layered MDP).
+ * Synchronises `stream` once to read the sweep count and residual. */
+mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol, int32_t max_sweeps,
+                     void *V, int16_t *policy, void *stream, mdp_solve_stats *stats);
+
+void mdp_model_free(mdp_model m);
+
+/* DO coefficients alone (step a1): Y[t][w][k] = sigma_h[k] * z with z from the
+ * Marsaglia polar method on Philox4x64-10 (Salmon et al., SC'11) counters
+ * (t, w, pair k/2, attempt) under key (seed, mdp_id).  Y: device [nt][N][K],
+ * float (FP32) or double (FP64_CHECK); the FP32 table is the FP64 draw rounded. */
+mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const double *sigma_h,
+                             uint64_t seed, uint64_t mdp_id, int32_t precision, void *Y,
+                             void *stream);
+
+/* ------------------------------------------------------------- batching --
+ * Builds and solves n independent MDPs (uneven sizes) with one persistent
+ * build launch over a shared work queue and one batched Bellman launch per
+ * sweep, all captured in a CUDA graph that is replayed on each call with the
+ * same shapes.  Arrays are host arrays of per-MDP descriptors; V[i] / policy[i]
+ * are device outputs as in mdp_solve (FP32 only).  Objective slot 0 of each
+ * MDP is solved with Jacobi to tol. */
+typedef struct {
+  mdp_env env;
+  mdp_grid grid;
+  mdp_actions actions;
+  int32_t N, subgrid_L;
+  int32_t objective;
+  void *V;
+  int16_t *policy;
+} mdp_batch_item;
+
+typedef struct mdp_batch_t *mdp_batch;
+
+mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n, double tol, mdp_batch *out);
+mdp_status mdp_batch_run(mdp_batch b, void *stream, int32_t *sweeps_h, double *ms);
+void mdp_batch_free(mdp_batch b);
+
+/* -------------------------------------------------------------- serving --
+ * Replanning server (on-board re-planning, Sec. V): environment fields stay
+ * resident on the device; requests carry a new start/target, a coefficient
+ * variance scale, a seed and N.  Requests are admitted while the HBM budget and
+ * free slots allow, run concurrently on per-slot streams (continuous batching),
+ * and retire independently. */
+typedef struct mdp_server_t *mdp_server;
+
+typedef struct {
+  int32_t env_id;
+  int32_t start_i, start_j;      /* reported entry of V / pi */
+  int32_t target_i, target_j;    /* lower-left corner of the target block */
+  int32_t target_w, target_h;    /* target block size in cells */
+  double sigma_scale;            /* multiplies the registered sigma_h */
+  uint64_t seed;
+  int32_t N;
+  int32_t objective;             /* mdp_objective */
+  double tol;
+} mdp_request;
+
+typedef struct {
+  int32_t status;                /* mdp_status of the request */
+  float V_start;                 /* V at (t = 0, start) */
+  int16_t pi_start;              /* policy at (t = 0, start) */
+  int32_t sweeps;
+  double latency_ms;             /* submit -> completion (host clock) */
+  double queue_ms;               /* submit -> admission */
+  int64_t device_bytes;          /* memory the request held */
+} mdp_result;
+
+/* hbm_budget_bytes: device memory the server may hold for requests;
+ * max_slots: concurrently running requests. */
+mdp_status mdp_serve_create(size_t hbm_budget_bytes, int32_t max_slots, mdp_server *out);
+/* Copies the environment's device arrays into server-owned device memory
+ * (FP32 only); sigma_h is copied too; coeffs must be NULL. */
+mdp_status mdp_env_register(mdp_server s, const mdp_env *env, const mdp_grid *grid,
+                            const mdp_actions *actions, int32_t subgrid_L, int32_t *env_id);
+mdp_status mdp_serve_submit(mdp_server s, const mdp_request *req, uint64_t *ticket);
+/* Waits up to timeout_ms (0 = do not wait) for the ticket; MDP_ERR_PENDING if
+ * not done.  Copies V and pi of the whole problem to V_h / pi_h when non-NULL
+ * (host [|S|+1] float / [|S|] int16), then releases the request. */
+mdp_status mdp_serve_poll(mdp_server s, uint64_t ticket, int32_t timeout_ms, mdp_result *out,
+                          float *V_h, int16_t *pi_h);
+mdp_status mdp_serve_stats(mdp_server s, int64_t *in_flight, int64_t *queued,
+                           int64_t *bytes_in_use);
+mdp_status mdp_serve_destroy(mdp_server s);
+
+const char *mdp_last_error(void);
+const char *mdp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDP_GB300_H */

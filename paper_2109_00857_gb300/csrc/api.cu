@@ -1,0 +1,483 @@
+// api.cu -- the C ABI of include/mdp.h: argument checks, device memory,
+// launch sequencing and status read-back for build, export, solve and the
+// standalone coefficient sampler.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <vector>
+
+#include "mdp_internal.cuh"
+
+namespace mdpgb {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+mdp_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorName(e) + " (" +
+            cudaGetErrorString(e) + ")");
+  return MDP_ERR_CUDA;
+}
+
+static mdp_status arg_fail(const std::string &msg) {
+  set_error("invalid argument: " + msg);
+  return MDP_ERR_ARG;
+}
+
+static std::mutex g_init_mu;
+static std::set<int> g_init_devices;
+
+int ensure_device_init() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (g_init_devices.count(dev)) return dev;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached for the next build
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_init_devices.insert(dev);
+  return dev;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+static int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static mdp_status check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    set_error("no usable CUDA device (this library has no CPU fallback)");
+    return MDP_ERR_CUDA;
+  }
+  if (ensure_device_init() < 0) {
+    set_error("cudaGetDevice failed");
+    return MDP_ERR_CUDA;
+  }
+  return MDP_OK;
+}
+
+// Host action table (Sec. II-A): a = f*Nh + h, theta = 2 pi h/Nh, F = Fmax (f+1)/NF.
+static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out) {
+  if (!ac) return arg_fail("actions is NULL");
+  const int A = ac->n_headings * ac->n_speeds;
+  if (ac->n_headings < 1 || ac->n_speeds < 1 || A > kMaxActions)
+    return arg_fail("n_headings * n_speeds must be in [1, 32]");
+  memset(t, 0, sizeof(*t));
+  for (int a = 0; a < A; ++a) {
+    double dx, dy, F;
+    if (ac->table_h) {
+      dx = ac->table_h[3 * a];
+      dy = ac->table_h[3 * a + 1];
+      F = ac->table_h[3 * a + 2];
+    } else {
+      const int f = a / ac->n_headings, h = a % ac->n_headings;
+      F = ac->f_max * (f + 1) / ac->n_speeds;
+      const double th = 2.0 * M_PI * h / ac->n_headings;
+      dx = F * std::cos(th);
+      dy = F * std::sin(th);
+    }
+    if (!std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(F))
+      return arg_fail("action table holds a non-finite value");
+    t->dx64[a] = dx;
+    t->dy64[a] = dy;
+    t->F64[a] = F;
+    t->dxl[a] = (float)(dx * lam);
+    t->dyl[a] = (float)(dy * lam);
+    t->F[a] = (float)F;
+  }
+  *A_out = A;
+  return MDP_OK;
+}
+
+struct Pinned {
+  unsigned long long *p = nullptr;
+  Pinned() { cudaMallocHost((void **)&p, sizeof(unsigned long long) * CNT_N * 2); }
+  ~Pinned() { if (p) cudaFreeHost(p); }
+};
+
+static void free_model_memory(mdp_model_t *m, cudaStream_t st) {
+  dev_free(m->pool, st);
+  dev_free(m->slice_off, st);
+  dev_free(m->nnz, st);
+  dev_free(m->R, st);
+  dev_free(m->cls, st);
+  dev_free(m->delta, st);
+  dev_free(m->Vtmp, st);
+  dev_free(m->cnt, st);
+  dev_free(m->solve_stats_d, st);
+  m->pool = nullptr;
+  m->slice_off = nullptr;
+  m->nnz = nullptr;
+  m->R = nullptr;
+  m->cls = nullptr;
+  m->delta = nullptr;
+  m->Vtmp = nullptr;
+  m->cnt = nullptr;
+  m->solve_stats_d = nullptr;
+}
+
+}  // namespace mdpgb
+
+using namespace mdpgb;
+
+extern "C" const char *mdp_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *mdp_version(void) { return "mdp_gb300 1.0 (sm_103a)"; }
+
+extern "C" mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const double *sigma_h,
+                                        uint64_t seed, uint64_t mdp_id, int32_t precision, void *Y,
+                                        void *stream) {
+  mdp_status s = check_device();
+  if (s != MDP_OK) return s;
+  if (nt < 1 || N < 1 || K < 1 || K > kMaxModes) return arg_fail("need nt, N >= 1 and 1 <= K <= 16");
+  if (!sigma_h || !Y) return arg_fail("sigma_h and Y must be non-NULL");
+  if (precision != MDP_FP32 && precision != MDP_FP64_CHECK) return arg_fail("precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  double *sig_d = nullptr;
+  unsigned long long *cap_d = nullptr;
+  MDP_CUDA_TRY(dev_alloc((void **)&sig_d, sizeof(double) * K, st));
+  MDP_CUDA_TRY(dev_alloc((void **)&cap_d, sizeof(unsigned long long), st));
+  MDP_CUDA_TRY(cudaMemcpyAsync(sig_d, sigma_h, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  MDP_CUDA_TRY(cudaMemsetAsync(cap_d, 0, sizeof(unsigned long long), st));
+  MDP_CUDA_TRY(launch_sample_coeffs(nt, N, K, sig_d, seed, mdp_id,
+                                    precision == MDP_FP64_CHECK ? (double *)Y : nullptr,
+                                    precision == MDP_FP32 ? (float *)Y : nullptr, cap_d, st));
+  unsigned long long capped = 0;
+  MDP_CUDA_TRY(cudaMemcpyAsync(&capped, cap_d, sizeof(capped), cudaMemcpyDeviceToHost, st));
+  dev_free(sig_d, st);
+  dev_free(cap_d, st);
+  MDP_CUDA_TRY(cudaStreamSynchronize(st));
+  (void)capped;  // a capped pair (probability ~1e-43 each) draws z = 0
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
+                                int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                                const mdp_build_opts *opts, void *stream, mdp_model *out) {
+  if (out) *out = nullptr;
+  mdp_status s = check_device();
+  if (s != MDP_OK) return s;
+  if (!env || !grid || !actions || !out || !objs_h) return arg_fail("NULL env/grid/actions/objs/out");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nt < 1) return arg_fail("grid sizes must be >= 1");
+  if (!(grid->dx > 0) || !(grid->dt > 0) || !std::isfinite(grid->dx) || !std::isfinite(grid->dt))
+    return arg_fail("dx and dt must be finite and > 0");
+  if (env->K < 0 || env->K > kMaxModes) return arg_fail("K must be in [0, 16]");
+  if (N < 1 || N > 65535) return arg_fail("N must be in [1, 65535]");
+  if (env->precision != MDP_FP32 && env->precision != MDP_FP64_CHECK) return arg_fail("precision");
+  if (n_obj < 1 || n_obj > 3) return arg_fail("n_obj must be in [1, 3]");
+  for (int o = 0; o < n_obj; ++o) {
+    if (objs_h[o] < 0 || objs_h[o] > 2) return arg_fail("unknown objective");
+    if (objs_h[o] == MDP_OBJ_NET_ENERGY && !env->gbar) return arg_fail("net energy needs gbar");
+  }
+  if (!env->vbar || !env->obstacle || !env->target || (env->K > 0 && !env->modes))
+    return arg_fail("vbar, modes, obstacle and target must be non-NULL");
+  if (env->K > 0 && !env->coeffs && !env->sigma_h) return arg_fail("need coeffs or sigma_h");
+  if (subgrid_L < 0 || subgrid_L > 255 || (subgrid_L > 0 && subgrid_L % 2 == 0))
+    return arg_fail("subgrid_L must be 0 (auto) or odd in [1, 255]");
+  const int row_cap = (opts && opts->row_cap > 0) ? opts->row_cap : 64;
+  if (row_cap > 255) return arg_fail("row_cap must be <= 255");
+  const int64_t Nc = (int64_t)grid->nx * grid->ny, nS = Nc * grid->nt;
+  if (nS > ((int64_t)1 << 40)) return arg_fail("grid too large");
+  const double lam = grid->dt / grid->dx;
+
+  ActionTable at;
+  int A = 0;
+  s = make_actions(actions, lam, &at, &A);
+  if (s != MDP_OK) return s;
+  const int prec = env->precision;
+  const size_t fsz = prec == MDP_FP64_CHECK ? 8 : 4;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  mdp_model_t *m = new mdp_model_t();
+  memset(m, 0, sizeof(*m));
+  m->nx = grid->nx; m->ny = grid->ny; m->nt = grid->nt;
+  m->K = env->K; m->N = N; m->A = A; m->precision = prec; m->n_obj = n_obj;
+  for (int o = 0; o < n_obj; ++o) m->objs[o] = objs_h[o];
+  m->Nc = Nc; m->nS = nS; m->dx = grid->dx; m->dt = grid->dt;
+  m->A_pad = pow2_at_least(A);
+  m->spw = 32 / m->A_pad;
+  m->n_slices = (nS + m->spw - 1) / m->spw;
+  m->rows_pad = m->n_slices * 32;
+  m->row_cap = row_cap;
+  cudaGetDevice(&m->device);
+  RewardParams &rw = m->rw;
+  rw.c_f = actions->c_f; rw.c_r = actions->c_r; rw.r_term = actions->r_term;
+  rw.r_out = actions->r_outbound; rw.dt = grid->dt; rw.dx = grid->dx; rw.n_obj = n_obj;
+  for (int o = 0; o < n_obj; ++o) rw.objs[o] = objs_h[o];
+
+  auto fail = [&](mdp_status code) {
+    free_model_memory(m, st);
+    delete m;
+    return code;
+  };
+#define TRY(expr)                                   \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return fail(cuda_fail(_e, #expr)); \
+  } while (0)
+
+  // -- coefficients: caller table or Philox draw (step a1)
+  const void *Y = env->coeffs;
+  void *Yown = nullptr;
+  double *sig_d = nullptr;
+  TRY(dev_alloc((void **)&m->cnt, sizeof(unsigned long long) * CNT_N, st));
+  TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  cudaEventRecord(ev0, st);
+  if (!Y && env->K > 0) {
+    TRY(dev_alloc(&Yown, fsz * (size_t)grid->nt * N * env->K, st));
+    TRY(dev_alloc((void **)&sig_d, sizeof(double) * env->K, st));
+    TRY(cudaMemcpyAsync(sig_d, env->sigma_h, sizeof(double) * env->K, cudaMemcpyHostToDevice, st));
+    TRY(launch_sample_coeffs(grid->nt, N, env->K, sig_d, env->seed, env->mdp_id,
+                             prec == MDP_FP64_CHECK ? (double *)Yown : nullptr,
+                             prec == MDP_FP32 ? (float *)Yown : nullptr, m->cnt + CNT_CAPPED, st));
+    Y = Yown;
+  }
+
+  // -- sub-grid side: given, or from the component-wise field extremes (Sec. III-B)
+  int L = subgrid_L;
+  if (L == 0) {
+    const int K = env->K;
+    unsigned int *ex = nullptr;
+    const int nex = 2 + 2 * K + K;
+    TRY(dev_alloc((void **)&ex, sizeof(unsigned int) * nex, st));
+    TRY(cudaMemsetAsync(ex, 0, sizeof(unsigned int) * nex, st));
+    TRY(launch_absmax(env->vbar, prec, nS * 2, 1, 1, 2, ex, st));
+    if (K > 0) {
+      TRY(launch_absmax(env->modes, prec, nS * K * 2, K, Nc, 2, ex + 2, st));
+      TRY(launch_absmax(Y, prec, (int64_t)grid->nt * N * K, K, 1, 1, ex + 2 + 2 * K, st));
+    }
+    std::vector<unsigned int> hx(nex);
+    TRY(cudaMemcpyAsync(hx.data(), ex, sizeof(unsigned int) * nex, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    dev_free(ex, st);
+    auto f = [&](int i) { float v; memcpy(&v, &hx[i], 4); return (double)v; };
+    double wmax[2] = {f(0), f(1)};
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < 2; ++c) wmax[c] += f(2 + 2 * K + k) * f(2 + 2 * k + c);
+    double amax[2] = {0, 0};
+    for (int a = 0; a < A; ++a) {
+      amax[0] = std::max(amax[0], std::fabs(at.dx64[a]));
+      amax[1] = std::max(amax[1], std::fabs(at.dy64[a]));
+    }
+    int h = 0;
+    for (int c = 0; c < 2; ++c) {
+      // |offset| <= ceil(1/2 + lam (max|v| + max|a|)), plus one cell of buffer
+      const int hc = (int)std::ceil(0.5 + lam * (wmax[c] + amax[c]) * (1.0 + 1e-6)) + 1;
+      h = std::max(h, hc);
+    }
+    if (2 * h + 1 > 255) return fail(arg_fail("automatic sub-grid would exceed 255 cells"));
+    L = 2 * h + 1;
+  }
+  m->L = L;
+  m->h = (L - 1) / 2;
+  m->nbins = L * L;
+
+  // -- model memory
+  const int Wmax = std::min(row_cap, m->nbins + 1);
+  uint64_t cap_cols = (uint64_t)m->n_slices * (uint64_t)Wmax;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const uint64_t budget_cols = (uint64_t)(0.6 * (double)free_b) / 128;
+  if (cap_cols > budget_cols) cap_cols = budget_cols;
+  if (cap_cols < 1) cap_cols = 1;
+  TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+  TRY(dev_alloc((void **)&m->slice_off, sizeof(uint32_t) * (size_t)m->n_slices, st));
+  TRY(dev_alloc((void **)&m->nnz, (size_t)m->rows_pad, st));
+  TRY(dev_alloc(&m->R, fsz * (size_t)m->rows_pad * n_obj, st));
+  TRY(dev_alloc((void **)&m->cls, (size_t)nS, st));
+  TRY(dev_alloc((void **)&m->delta, sizeof(int32_t) * (size_t)m->nbins, st));
+  TRY(launch_prepare(env->obstacle, env->target, m->cls, grid->nx, grid->ny, grid->nt, m->delta, L, st));
+
+  BuildArgs ba;
+  memset(&ba, 0, sizeof(ba));
+  ba.nx = grid->nx; ba.ny = grid->ny; ba.nt = grid->nt; ba.K = env->K; ba.N = N; ba.A = A;
+  ba.A_pad = m->A_pad; ba.spw = m->spw; ba.L = L; ba.h = m->h; ba.nbins = m->nbins;
+  ba.row_cap = Wmax; ba.Nc = Nc; ba.nS = nS; ba.n_slices = m->n_slices; ba.rows_pad = m->rows_pad;
+  ba.lam = (float)lam;
+  ba.vbar = env->vbar; ba.modes = env->modes; ba.Y = Y; ba.gbar = env->gbar; ba.cls = m->cls;
+  ba.act = at; ba.rw = rw;
+  ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.nnz = m->nnz;
+  ba.R = m->R; ba.cnt = m->cnt;
+  ba.slice_begin = 0; ba.slice_end = m->n_slices;
+  int threads = (opts && opts->threads > 0) ? opts->threads : 256;
+  if (threads % 64 != 0 || threads > 512) return fail(arg_fail("threads must be a multiple of 64, <= 512"));
+  int chunk = (opts && opts->chunk > 0) ? opts->chunk : 1024;
+  if (chunk > N) chunk = N;
+  ba.chunk = chunk;
+  if (prec == MDP_FP64_CHECK) {
+    TRY(launch_build_fp64(ba, st));
+  } else {
+    TRY(launch_build_fp32(ba, threads, num_sms(), st));
+  }
+  cudaEventRecord(ev1, st);
+  static thread_local Pinned pin;
+  if (!pin.p) return fail(cuda_fail(cudaErrorMemoryAllocation, "cudaMallocHost"));
+  TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+  if (Yown) dev_free(Yown, st);
+  if (sig_d) dev_free(sig_d, st);
+  TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  m->build_ms = ms;
+  const unsigned long long *c = pin.p;
+  if (c[CNT_OVERFLOW]) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%llu landing(s)/row(s) left the %dx%d neighbouring sub-grid; use a larger subgrid_L",
+             c[CNT_OVERFLOW], L, L);
+    set_error(buf);
+    return fail(MDP_ERR_SUBGRID_OVERFLOW);
+  }
+  if (c[CNT_ROW_CAP]) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%llu row(s) had more than %d successors (raise row_cap)", c[CNT_ROW_CAP], Wmax);
+    set_error(buf);
+    return fail(MDP_ERR_ELL_OVERFLOW);
+  }
+  if (c[CNT_POOL_FULL]) {
+    set_error("entry pool capacity exhausted (device memory budget)");
+    return fail(MDP_ERR_OOM);
+  }
+  m->pool_cols = c[CNT_POOL_COLS];
+  m->nnz_total = (int64_t)c[CNT_NNZ];
+  m->max_row_nnz = (int32_t)c[CNT_MAXROW];
+  m->samples = (int64_t)c[CNT_SAMPLES];
+  // -- compaction: the bump-allocated columns are contiguous, so shrink the pool
+  if (!(opts && opts->no_compact) && m->pool_cols < cap_cols) {
+    uint32_t *np = nullptr;
+    TRY(dev_alloc((void **)&np, (size_t)std::max<uint64_t>(m->pool_cols, 1) * 128, st));
+    if (m->pool_cols) TRY(cudaMemcpyAsync(np, m->pool, (size_t)m->pool_cols * 128, cudaMemcpyDeviceToDevice, st));
+    dev_free(m->pool, st);
+    m->pool = np;
+    cap_cols = std::max<uint64_t>(m->pool_cols, 1);
+  }
+  m->device_bytes = (int64_t)cap_cols * 128 + 4 * m->n_slices + m->rows_pad + (int64_t)fsz * m->rows_pad * n_obj +
+                    nS + 4 * m->nbins + 8 * CNT_N;
+  *out = m;
+#undef TRY
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *o) {
+  if (!m || !o) return arg_fail("NULL model or info");
+  memset(o, 0, sizeof(*o));
+  o->n_states = m->nS;
+  o->A = m->A;
+  o->N = m->N;
+  o->L = m->L;
+  o->n_obj = m->n_obj;
+  for (int i = 0; i < m->n_obj; ++i) o->objs[i] = m->objs[i];
+  o->precision = m->precision;
+  o->rows = m->nS * m->A;
+  o->nnz = m->nnz_total;
+  o->max_row_nnz = m->max_row_nnz;
+  o->pool_columns = (int64_t)m->pool_cols;
+  o->device_bytes = m->device_bytes + (m->Vtmp ? (int64_t)(m->nS + 1) * (m->precision ? 8 : 4) : 0);
+  o->samples = m->samples;
+  o->build_ms = m->build_ms;
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_export_csr(mdp_model m, int32_t obj, int64_t *rowptr, int64_t *col,
+                                     int32_t *count, void *R, void *stream) {
+  if (!m || !rowptr) return arg_fail("NULL model or rowptr");
+  if (obj < 0 || obj >= m->n_obj) return arg_fail("objective slot out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  MDP_CUDA_TRY(launch_export(m, obj, rowptr, col, count, R, st));
+  MDP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol,
+                                int32_t max_sweeps, void *V, int16_t *policy, void *stream,
+                                mdp_solve_stats *stats) {
+  if (!m || !V || !policy) return arg_fail("NULL model, V or policy");
+  if (obj < 0 || obj >= m->n_obj) return arg_fail("objective slot out of range");
+  if (method != MDP_SOLVE_JACOBI && method != MDP_SOLVE_LAYERED) return arg_fail("method");
+  if (!(tol >= 0) && !(tol < 0)) return arg_fail("tol is NaN");
+  if (max_sweeps < 0) return arg_fail("max_sweeps must be >= 0");
+  if (max_sweeps == 0) max_sweeps = m->nt + 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t fsz = m->precision == MDP_FP64_CHECK ? 8 : 4;
+  const size_t vbytes = fsz * (size_t)(m->nS + 1);
+  if (method == MDP_SOLVE_JACOBI && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
+  double *sd = nullptr;
+  MDP_CUDA_TRY(dev_alloc((void **)&sd, sizeof(double) * (4 + (size_t)max_sweeps), st));
+  MDP_CUDA_TRY(cudaMemsetAsync(sd, 0, sizeof(double) * 4, st));
+  MDP_CUDA_TRY(cudaMemsetAsync(V, 0, vbytes, st));
+  if (method == MDP_SOLVE_JACOBI) MDP_CUDA_TRY(cudaMemsetAsync(m->Vtmp, 0, vbytes, st));
+  SolveArgs a;
+  a.pool = m->pool; a.slice_off = m->slice_off; a.nnz = m->nnz;
+  a.R = static_cast<const char *>(m->R) + fsz * (size_t)obj * m->rows_pad;
+  a.cls = m->cls; a.delta = m->delta;
+  a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;
+  a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.tol = tol;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  cudaError_t ce;
+  if (method == MDP_SOLVE_JACOBI) ce = launch_jacobi(a, m->precision, max_sweeps, V, m->Vtmp, policy, sd, st);
+  else ce = launch_layered(a, m->precision, m->nt, V, policy, sd, st);
+  cudaEventRecord(e1, st);
+  double hs[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hs, sd, sizeof(hs), cudaMemcpyDeviceToHost, st);
+  dev_free(sd, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(ce, "mdp_solve");
+  if (stats) {
+    if (method == MDP_SOLVE_JACOBI) {
+      stats->sweeps = (int32_t)hs[0];
+      stats->residual = hs[1];
+    } else {
+      stats->sweeps = 1;
+      stats->residual = 0.0;
+    }
+    stats->solve_ms = ms;
+    stats->backups = (int64_t)stats->sweeps * m->nS * m->A;
+  }
+  return MDP_OK;
+}
+
+extern "C" void mdp_model_free(mdp_model m) {
+  if (!m) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != m->device) cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  free_model_memory(m, 0);
+  if (cur != m->device) cudaSetDevice(cur);
+  delete m;
+}

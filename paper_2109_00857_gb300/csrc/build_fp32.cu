@@ -1,0 +1,246 @@
+// build_fp32.cu -- production FP32 MDP build (steps a2-a6), one fused kernel.
+//
+// Persistent CTAs pull slices (32 internal rows = spw states x A_pad actions)
+// from a device work queue.  Per slice and per chunk of realizations:
+//   phase A  threads form the DO velocity of their (state, realization),
+//            w = vbar + sum_k Y_k v~_k (Sec. II-C), once for all actions, and
+//            stage u = 1/2 + w dt/dx (position relative to the cell's lower
+//            edge after the flow, in cells) in shared memory; the per-state
+//            extremes of u bound every landing offset of every action.
+//   phase B  lane l of every warp owns row (state q, action a) = (l / A_pad,
+//            l % A_pad).  For each staged realization it forms
+//            floor(u + d_a dt/dx) in x and y (Sec. II-A move, cell()) and
+//            counts the sub-grid bin with a shared-memory reduction into
+//            hist[bin][l]: a lane only ever touches its own bank, so the
+//            counting has no bank or address conflicts within a warp.
+//   emit     warp 0 turns each lane's column into sparse (bin, count) entries,
+//            folds out-of-domain / obstacle landings into the sink and forms
+//            R(s,a) from the counts (build_common.cuh).
+// Landing offsets are checked against the sub-grid from the per-state extremes
+// before any count is made (floor and rounded addition are monotone, so the
+// extremes of u give the exact extremes of every action's offsets); a state
+// whose offsets leave the sub-grid is reported as overflow and counts nothing.
+#include "build_common.cuh"
+
+namespace mdpgb {
+
+constexpr float kMagic = 12582912.0f;         // 1.5 * 2^23: floor via round-down add
+constexpr uint32_t kMagicBits = 0x4B400000u;  // bit pattern of kMagic
+
+__device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+__device__ __forceinline__ float warp_min(float v, int from) {
+  for (int off = 16; off >= from; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v, int from) {
+  for (int off = 16; off >= from; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+template <int KT>
+__device__ __forceinline__ void load_y(const float *__restrict__ yw, float (&y)[KT > 0 ? KT : 1]) {
+  if constexpr (KT > 0 && (KT % 4) == 0) {
+#pragma unroll
+    for (int k = 0; k < KT; k += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(yw + k));
+      y[k] = v.x; y[k + 1] = v.y; y[k + 2] = v.z; y[k + 3] = v.w;
+    }
+  } else if constexpr (KT > 0) {
+#pragma unroll
+    for (int k = 0; k < KT; ++k) y[k] = __ldg(yw + k);
+  }
+}
+
+// KT > 0: the number of modes is a compile-time constant; KT == 0: runtime K.
+template <int KT>
+__global__ void __launch_bounds__(512) build_fp32_kernel(BuildArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *hist = smem;                                             // [nbins][32]
+  uint32_t *stage = hist + (size_t)a.nbins * 32;                     // [row_cap][32]
+  float2 *ubuf = reinterpret_cast<float2 *>(stage + (size_t)a.row_cap * 32);  // [chunk][spw]
+  float *red = reinterpret_cast<float *>(ubuf + (size_t)a.chunk * a.spw);    // [nwarps][spw][4]
+  __shared__ long long s_slice;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int K = KT > 0 ? KT : a.K;
+  for (int i = tid; i < a.nbins * 32; i += blockDim.x) hist[i] = 0;
+
+  // lane role (phase B / emit): row (q_l, a_l) of the slice
+  const int q_l = lane / a.A_pad, a_l = lane % a.A_pad;
+  const bool act_ok = a_l < a.A;
+  const float dxl = act_ok ? a.act.dxl[a_l] : 0.f;
+  const float dyl = act_ok ? a.act.dyl[a_l] : 0.f;
+  // hist byte address of (bin(fx, fy), lane) for magic-biased floor bits bx, by:
+  //   ((by - M + h) * L + (bx - M + h)) * 128 + lane * 4 + hist_base  (mod 2^32)
+  const uint32_t rowstride = (uint32_t)a.L * 128u;
+  const uint32_t hbase = smem_u32(hist) + (uint32_t)lane * 4u +
+                         ((uint32_t)a.h * (uint32_t)a.L + (uint32_t)a.h) * 128u -
+                         kMagicBits * rowstride - kMagicBits * 128u;
+  // thread role (phase A): state q_t of the slice, realizations w0, w0 + wstride, ...
+  const int q_t = tid % a.spw;
+  const int w0 = tid / a.spw, wstride = blockDim.x / a.spw;
+  const float lam = a.lam;
+  const float *Yall = static_cast<const float *>(a.Y);
+  const float *vbar = static_cast<const float *>(a.vbar);
+  const float *modes = static_cast<const float *>(a.modes);
+  __syncthreads();
+
+  for (;;) {
+    if (tid == 0) s_slice = a.slice_begin + (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+    __syncthreads();
+    const int64_t sl = s_slice;
+    if (sl >= a.slice_end) break;
+
+    const int64_t s_l = sl * a.spw + q_l;
+    int kind_l = state_kind(a, s_l);
+    if (!act_ok) kind_l = KIND_NONE;
+    const int64_t s_t = sl * a.spw + q_t;
+    const int kind_t = state_kind(a, s_t);
+    const int any_sample = __syncthreads_or(kind_t == KIND_SAMPLE);
+
+    float run_mnx = INFINITY, run_mxx = -INFINITY, run_mny = INFINITY, run_mxy = -INFINITY;
+    bool active = (kind_l == KIND_SAMPLE);
+    if (any_sample) {
+      // per-thread DO mean and modes at (t, cell) of state q_t
+      float phx[KT > 0 ? KT : kMaxModes], phy[KT > 0 ? KT : kMaxModes];
+      float vbx = 0.f, vby = 0.f;
+      const float *Yt = Yall;
+      if (kind_t == KIND_SAMPLE) {
+        const int64_t t = s_t / a.Nc, c = s_t % a.Nc;
+        vbx = vbar[2 * s_t];
+        vby = vbar[2 * s_t + 1];
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : kMaxModes); ++k) {
+          if (KT == 0 && k >= K) break;
+          const float2 ph = *reinterpret_cast<const float2 *>(modes + 2 * ((t * K + k) * a.Nc + c));
+          phx[k] = ph.x;
+          phy[k] = ph.y;
+        }
+        Yt = Yall + (size_t)t * a.N * K;
+      }
+      for (int c0 = 0; c0 < a.N; c0 += a.chunk) {
+        const int cn = min(a.chunk, a.N - c0);
+        // ---- phase A: velocities of this chunk
+        float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+        if (kind_t == KIND_SAMPLE) {
+          for (int w = w0; w < cn; w += wstride) {
+            const float *yw = Yt + (size_t)(c0 + w) * K;
+            float wx = vbx, wy = vby;
+            if constexpr (KT > 0) {
+              float y[KT];
+              load_y<KT>(yw, y);
+#pragma unroll
+              for (int k = 0; k < KT; ++k) {
+                wx = fmaf(y[k], phx[k], wx);
+                wy = fmaf(y[k], phy[k], wy);
+              }
+            } else {
+              for (int k = 0; k < K; ++k) {
+                const float yk = __ldg(yw + k);
+                wx = fmaf(yk, phx[k], wx);
+                wy = fmaf(yk, phy[k], wy);
+              }
+            }
+            float ux = fmaf(wx, lam, 0.5f), uy = fmaf(wy, lam, 0.5f);
+            // a non-finite velocity must not reach the bin arithmetic: push it far
+            // outside every sub-grid so the extreme check reports overflow
+            if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
+            if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+            ubuf[(size_t)w * a.spw + q_t] = make_float2(ux, uy);
+            mnx = fminf(mnx, ux); mxx = fmaxf(mxx, ux);
+            mny = fminf(mny, uy); mxy = fmaxf(mxy, uy);
+          }
+        }
+        // extremes per state q over this chunk: lanes with equal q share lane % spw
+        mnx = warp_min(mnx, a.spw); mxx = warp_max(mxx, a.spw);
+        mny = warp_min(mny, a.spw); mxy = warp_max(mxy, a.spw);
+        if (lane < a.spw) {
+          float *r = red + ((size_t)warp * a.spw + lane) * 4;
+          r[0] = mnx; r[1] = mxx; r[2] = mny; r[3] = mxy;
+        }
+        __syncthreads();
+        float cmnx = INFINITY, cmxx = -INFINITY, cmny = INFINITY, cmxy = -INFINITY;
+        for (int wv = 0; wv < nwarps; ++wv) {
+          const float *r = red + ((size_t)wv * a.spw + q_l) * 4;
+          cmnx = fminf(cmnx, r[0]); cmxx = fmaxf(cmxx, r[1]);
+          cmny = fminf(cmny, r[2]); cmxy = fmaxf(cmxy, r[3]);
+        }
+        run_mnx = fminf(run_mnx, cmnx); run_mxx = fmaxf(run_mxx, cmxx);
+        run_mny = fminf(run_mny, cmny); run_mxy = fmaxf(run_mxy, cmxy);
+        if (active) {
+          const int lox = (int)floorf(cmnx + dxl), hix = (int)floorf(cmxx + dxl);
+          const int loy = (int)floorf(cmny + dyl), hiy = (int)floorf(cmxy + dyl);
+          if (lox < -a.h || hix > a.h || loy < -a.h || hiy > a.h) active = false;
+        }
+        // ---- phase B: count landings of this chunk
+        if (active) {
+          const float2 *ub = ubuf + q_l;
+#pragma unroll 4
+          for (int w = warp; w < cn; w += nwarps) {
+            const float2 u = ub[(size_t)w * a.spw];
+            const uint32_t bx = __float_as_uint(__fadd_rd(u.x + dxl, kMagic));
+            const uint32_t by = __float_as_uint(__fadd_rd(u.y + dyl, kMagic));
+            red_add_shared(by * rowstride + bx * 128u + hbase, 1u);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- emit (warp 0)
+    if (warp == 0) {
+      int lox = 0, hix = -1, loy = 0, hiy = -1;
+      if (kind_l == KIND_SAMPLE && run_mnx <= run_mxx) {
+        lox = (int)floorf(run_mnx + dxl); hix = (int)floorf(run_mxx + dxl);
+        loy = (int)floorf(run_mny + dyl); hiy = (int)floorf(run_mxy + dyl);
+      }
+      const bool row_ok = active || kind_l != KIND_SAMPLE;
+      if (kind_l == KIND_SAMPLE) {
+        if (!row_ok) atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
+        else atomicAdd(&a.cnt[CNT_SAMPLES], (unsigned long long)a.N);
+      }
+      emit_slice<float>(a, hist, stage, sl, kind_l, row_ok, lox, hix, loy, hiy);
+    }
+    __syncthreads();
+  }
+}
+
+static size_t fp32_smem_bytes(const BuildArgs &a, int threads) {
+  return (size_t)a.nbins * 32 * 4 + (size_t)a.row_cap * 32 * 4 + (size_t)a.chunk * a.spw * 8 +
+         (size_t)(threads / 32) * a.spw * 16;
+}
+
+template <int KT>
+static cudaError_t launch_kt(const BuildArgs &a, int threads, int sms, cudaStream_t st) {
+  const size_t smem = fp32_smem_bytes(a, threads);
+  cudaError_t e = cudaFuncSetAttribute(build_fp32_kernel<KT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_fp32_kernel<KT>, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t blocks = (int64_t)sms * per_sm;
+  const int64_t work = a.slice_end - a.slice_begin;
+  if (blocks > work) blocks = work > 0 ? work : 1;
+  build_fp32_kernel<KT><<<(unsigned)blocks, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_fp32(const BuildArgs &a, int threads, int sms, cudaStream_t st) {
+  switch (a.K) {
+    case 1: return launch_kt<1>(a, threads, sms, st);
+    case 2: return launch_kt<2>(a, threads, sms, st);
+    case 3: return launch_kt<3>(a, threads, sms, st);
+    case 4: return launch_kt<4>(a, threads, sms, st);
+    case 5: return launch_kt<5>(a, threads, sms, st);
+    case 6: return launch_kt<6>(a, threads, sms, st);
+    case 8: return launch_kt<8>(a, threads, sms, st);
+    default: return launch_kt<0>(a, threads, sms, st);
+  }
+}
+
+}  // namespace mdpgb

@@ -1,0 +1,163 @@
+// mdp_internal.cuh -- internal types and device helpers of libmdp_gb300.
+//
+// Model layout in HBM (sliced ELLPACK, one slice per 32 internal rows):
+//   internal row   ir = s * A_pad + a          (A_pad = A rounded up to a power of two <= 32)
+//   slice          sl = ir / 32 = s / spw      (spw = 32 / A_pad states per slice)
+//   lane           l  = ir % 32 = (s % spw) * A_pad + a
+//   entries        pool[(slice_off[sl] + k) * 32 + l], k < nnz[ir], one 32-bit word each:
+//                  bits 0..15 sub-grid bin b = (dj+h)*L + (di+h)  (0xFFFF = sink),
+//                  bits 16..31 count (realizations landing there, <= N <= 65535)
+//   successor      s' = s + Nc + delta[b]      (delta[b] = dj*Nx + di), sink s' = |S|
+//   R              R[o * rows_pad + ir]        (float or double), rows_pad = n_slices * 32
+// Warps read a slice column (32 lanes x 4 B = 128 B) per k: fully coalesced.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mdp.h"
+
+namespace mdpgb {
+
+constexpr int kMaxActions = 32;
+constexpr int kMaxModes = 16;
+constexpr uint32_t kSinkBin = 0xFFFFu;
+constexpr uint32_t kNoSlice = 0xFFFFFFFFu;
+
+// cell class bits, [nt][ny][nx]
+enum : uint8_t { CLS_FREE = 0, CLS_OBSTACLE = 1, CLS_TARGET = 2 };
+
+// device status counters (unsigned long long each)
+enum {
+  CNT_POOL_COLS = 0,     // 32-entry columns handed out
+  CNT_OVERFLOW = 1,      // (s,a) rows / samples that left the sub-grid
+  CNT_ROW_CAP = 2,       // rows longer than row_cap
+  CNT_POOL_FULL = 3,     // slices that did not fit the pool
+  CNT_CAPPED = 4,        // polar pairs that hit the attempt cap
+  CNT_WORK = 5,          // dynamic work-queue head
+  CNT_SAMPLES = 6,       // landing evaluations performed
+  CNT_NNZ = 7,           // stored entries (sink included)
+  CNT_MAXROW = 8,        // widest row
+  CNT_N = 16
+};
+
+struct ActionTable {
+  float dxl[kMaxActions];   // F cos(theta) * dt/dx   (FP32 kinematics, grid units)
+  float dyl[kMaxActions];
+  float F[kMaxActions];
+  double dx64[kMaxActions];  // F cos(theta), F sin(theta), F in FP64 (check mode)
+  double dy64[kMaxActions];
+  double F64[kMaxActions];
+};
+
+struct RewardParams {
+  double c_f, c_r, r_term, r_out, dt, dx;
+  int32_t n_obj;
+  int32_t objs[3];
+};
+
+// Everything the build kernels need, passed by value.
+struct BuildArgs {
+  int32_t nx, ny, nt, K, N, A, A_pad, spw, L, h, nbins, row_cap;
+  int64_t Nc, nS, n_slices, rows_pad;
+  float lam;                 // dt / dx
+  const void *vbar, *modes, *Y, *gbar;
+  const uint8_t *cls;
+  ActionTable act;
+  RewardParams rw;
+  uint32_t *pool;
+  uint64_t pool_cap_cols;
+  uint32_t *slice_off;
+  uint8_t *nnz;
+  void *R;
+  unsigned long long *cnt;
+  int32_t chunk;             // realizations per staged pass (FP32)
+  int64_t slice_begin, slice_end;  // work range [begin, end)
+};
+
+struct mdp_model_impl;
+
+}  // namespace mdpgb
+
+struct mdp_model_t {
+  int32_t nx, ny, nt, K, N, A, A_pad, spw, L, h, nbins, row_cap, precision, n_obj;
+  int32_t objs[3];
+  int64_t Nc, nS, n_slices, rows_pad;
+  double dx, dt;
+  mdpgb::RewardParams rw;
+  // device memory owned by the model
+  uint32_t *pool;
+  uint64_t pool_cols;         // columns in use (after compaction: capacity == in use)
+  uint32_t *slice_off;
+  uint8_t *nnz;
+  void *R;                    // [n_obj][rows_pad]
+  uint8_t *cls;               // [nt][ny][nx]
+  int32_t *delta;             // [nbins]
+  void *Vtmp;                 // [nS+1] Jacobi ping-pong partner
+  unsigned long long *cnt;    // [CNT_N]
+  double *solve_stats_d;      // [4] device scalars for the solver
+  int64_t device_bytes;
+  int64_t nnz_total;
+  int32_t max_row_nnz;
+  int64_t samples;
+  double build_ms;
+  int device;
+};
+
+namespace mdpgb {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string &msg);
+mdp_status cuda_fail(cudaError_t e, const char *what);
+#define MDP_CUDA_TRY(expr)                                    \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::mdpgb::cuda_fail(_e, #expr); \
+  } while (0)
+
+// ---------------------------------------------------------------- memory --
+// Stream-ordered allocations from the device's default memory pool, kept
+// cached by the pool between builds (release threshold raised at init).
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+int ensure_device_init();
+
+// ----------------------------------------------------------- launches ----
+// sampler (FP64 draw; FP32 copy is the FP64 value rounded)
+cudaError_t launch_sample_coeffs(int nt, int N, int K, const double *sigma_d, uint64_t seed,
+                                 uint64_t mdp_id, double *Y64, float *Y32,
+                                 unsigned long long *capped, cudaStream_t st);
+// build
+cudaError_t launch_build_fp32(const BuildArgs &a, int threads, int sms, cudaStream_t st);
+cudaError_t launch_build_fp64(const BuildArgs &a, cudaStream_t st);
+// cell classes + sub-grid delta table
+cudaError_t launch_prepare(const uint8_t *obstacle, const uint8_t *target, uint8_t *cls,
+                           int nx, int ny, int nt, int32_t *delta, int L, cudaStream_t st);
+// out[g*C + c] = max |x| over group g, component c of data laid out
+// [outer][G][inner][C] (n elements); out holds float bit patterns, zeroed by the caller
+cudaError_t launch_absmax(const void *x, int precision, int64_t n, int G, int64_t inner, int C,
+                          unsigned int *out, cudaStream_t st);
+// solve
+struct SolveArgs {
+  const uint32_t *pool;
+  const uint32_t *slice_off;
+  const uint8_t *nnz;
+  const void *R;              // objective slot base
+  const uint8_t *cls;
+  const int32_t *delta;
+  int64_t nS, Nc, n_slices;
+  int32_t A, A_pad, spw, N;
+  double tol;
+};
+cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
+                          int16_t *policy, double *stats_d, cudaStream_t st);
+cudaError_t launch_layered(const SolveArgs &a, int precision, int nt, void *V, int16_t *policy,
+                           double *stats_d, cudaStream_t st);
+// export
+cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_t *col,
+                          int32_t *count, void *R, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace mdpgb

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libmdp_gb300.so (include/mdp.h), same names as the C ABI.
+
+Argument marshalling only: every step of the build and the solve runs in the
+library's CUDA kernels.  torch provides device memory and streams.  There is no
+CPU fallback: if the library is missing or no CUDA device is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmdp_gb300.so")
+
+MDP_OK = 0
+STATUS = {0: "MDP_OK", -1: "MDP_ERR_ARG", -2: "MDP_ERR_OOM", -3: "MDP_ERR_SUBGRID_OVERFLOW",
+          -4: "MDP_ERR_ELL_OVERFLOW", -5: "MDP_ERR_TIMEOUT", -6: "MDP_ERR_CUDA",
+          -7: "MDP_ERR_BUDGET", -8: "MDP_ERR_CANCELLED", -9: "MDP_ERR_NOT_FOUND",
+          -10: "MDP_ERR_PENDING"}
+MDP_OBJ_TIME, MDP_OBJ_ENERGY, MDP_OBJ_NET_ENERGY = 0, 1, 2
+MDP_FP32, MDP_FP64_CHECK = 0, 1
+MDP_SOLVE_JACOBI, MDP_SOLVE_LAYERED = 0, 1
+
+P = C.c_void_p
+
+
+class MdpGrid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nt", C.c_int32),
+                ("dx", C.c_double), ("dt", C.c_double)]
+
+
+class MdpActions(C.Structure):
+    _fields_ = [("n_headings", C.c_int32), ("n_speeds", C.c_int32), ("f_max", C.c_double),
+                ("table_h", P), ("c_f", C.c_double), ("c_r", C.c_double),
+                ("r_term", C.c_double), ("r_outbound", C.c_double)]
+
+
+class MdpEnv(C.Structure):
+    _fields_ = [("K", C.c_int32), ("precision", C.c_int32), ("vbar", P), ("modes", P),
+                ("coeffs", P), ("sigma_h", P), ("seed", C.c_uint64), ("mdp_id", C.c_uint64),
+                ("gbar", P), ("obstacle", P), ("target", P)]
+
+
+class MdpBuildOpts(C.Structure):
+    _fields_ = [("row_cap", C.c_int32), ("no_compact", C.c_int32), ("threads", C.c_int32),
+                ("chunk", C.c_int32)]
+
+
+class MdpModelInfo(C.Structure):
+    _fields_ = [("n_states", C.c_int64), ("A", C.c_int32), ("N", C.c_int32), ("L", C.c_int32),
+                ("n_obj", C.c_int32), ("objs", C.c_int32 * 3), ("precision", C.c_int32),
+                ("rows", C.c_int64), ("nnz", C.c_int64), ("max_row_nnz", C.c_int32),
+                ("pool_columns", C.c_int64), ("device_bytes", C.c_int64), ("samples", C.c_int64),
+                ("build_ms", C.c_double)]
+
+
+class MdpSolveStats(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("residual", C.c_double), ("solve_ms", C.c_double),
+                ("backups", C.c_int64)]
+
+
+class MdpBatchItem(C.Structure):
+    _fields_ = [("env", MdpEnv), ("grid", MdpGrid), ("actions", MdpActions), ("N", C.c_int32),
+                ("subgrid_L", C.c_int32), ("objective", C.c_int32), ("V", P), ("policy", P)]
+
+
+class MdpRequest(C.Structure):
+    _fields_ = [("env_id", C.c_int32), ("start_i", C.c_int32), ("start_j", C.c_int32),
+                ("target_i", C.c_int32), ("target_j", C.c_int32), ("target_w", C.c_int32),
+                ("target_h", C.c_int32), ("sigma_scale", C.c_double), ("seed", C.c_uint64),
+                ("N", C.c_int32), ("objective", C.c_int32), ("tol", C.c_double)]
+
+
+class MdpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("V_start", C.c_float), ("pi_start", C.c_int16),
+                ("sweeps", C.c_int32), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+# name -> (restype, argtypes); every symbol include/mdp.h declares
+SIGNATURES = {
+    "mdp_build": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P]),
+    "mdp_model_info": (C.c_int, [P, P]),
+    "mdp_export_csr": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
+    "mdp_solve": (C.c_int, [P, C.c_int32, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
+    "mdp_model_free": (None, [P]),
+    "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
+                                    C.c_int32, P, P]),
+    "mdp_batch_create": (C.c_int, [P, C.c_int32, C.c_double, P]),
+    "mdp_batch_run": (C.c_int, [P, P, P, P]),
+    "mdp_batch_free": (None, [P]),
+    "mdp_serve_create": (C.c_int, [C.c_size_t, C.c_int32, P]),
+    "mdp_env_register": (C.c_int, [P, P, P, P, C.c_int32, P]),
+    "mdp_serve_submit": (C.c_int, [P, P, P]),
+    "mdp_serve_poll": (C.c_int, [P, C.c_uint64, C.c_int32, P, P, P]),
+    "mdp_serve_stats": (C.c_int, [P, P, P, P]),
+    "mdp_serve_destroy": (C.c_int, [P]),
+    "mdp_last_error": (C.c_char_p, []),
+    "mdp_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+class MdpError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load the CUDA library.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmdp_gb300.so not found at {path}; run __graft_entry__.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != MDP_OK:
+        raise MdpError(code, where, load().mdp_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------- marshalling --
+class DeviceEnv:
+    """Device copies (torch tensors) of an inputs.Environment in one precision."""
+
+    def __init__(self, env, precision: int = MDP_FP32, device="cuda", with_coeffs: bool = False):
+        import torch
+        ft = torch.float64 if precision == MDP_FP64_CHECK else torch.float32
+        self.env, self.precision = env, precision
+        self.vbar = torch.as_tensor(np.ascontiguousarray(env.vbar)).to(device, ft).contiguous()
+        self.modes = torch.as_tensor(np.ascontiguousarray(env.modes)).to(device, ft).contiguous()
+        self.gbar = (torch.as_tensor(np.ascontiguousarray(env.gbar)).to(device, ft).contiguous()
+                     if env.gbar is not None else None)
+        self.obstacle = torch.as_tensor(np.ascontiguousarray(env.obstacle, dtype=np.uint8)).to(device)
+        self.target = torch.as_tensor(np.ascontiguousarray(env.target, dtype=np.uint8)).to(device)
+        self.coeffs = None
+        if env.Y is not None:
+            self.coeffs = torch.as_tensor(np.ascontiguousarray(env.Y)).to(device, ft).contiguous()
+        self.sigma = np.ascontiguousarray(env.sigma, dtype=np.float64)
+        self.table = np.ascontiguousarray(env.actions, dtype=np.float64)
+
+    def c_env(self) -> MdpEnv:
+        e = MdpEnv()
+        e.K = self.env.K
+        e.precision = self.precision
+        e.vbar, e.modes = _ptr(self.vbar), _ptr(self.modes)
+        e.coeffs = _ptr(self.coeffs)
+        e.sigma_h = self.sigma.ctypes.data_as(P).value
+        e.seed, e.mdp_id = int(self.env.seed), int(self.env.mdp_id)
+        e.gbar = _ptr(self.gbar)
+        e.obstacle, e.target = _ptr(self.obstacle), _ptr(self.target)
+        return e
+
+    def c_grid(self) -> MdpGrid:
+        g = MdpGrid()
+        g.nx, g.ny, g.nt, g.dx, g.dt = self.env.nx, self.env.ny, self.env.nt, self.env.dx, self.env.dt
+        return g
+
+    def c_actions(self) -> MdpActions:
+        a = MdpActions()
+        a.n_headings, a.n_speeds = self.env.A, 1
+        a.f_max = float(self.table[:, 2].max())
+        a.table_h = self.table.ctypes.data_as(P).value
+        a.c_f, a.c_r = self.env.c_f, self.env.c_r
+        a.r_term, a.r_outbound = self.env.r_term, self.env.r_outbound
+        return a
+
+
+class Model:
+    """Owner of an mdp_model handle."""
+
+    def __init__(self, handle: int, precision: int):
+        self.handle = handle
+        self.precision = precision
+
+    def info(self) -> MdpModelInfo:
+        return mdp_model_info(self)
+
+    def free(self):
+        if self.handle:
+            load().mdp_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- calls --
+def mdp_build(denv: DeviceEnv, N: Optional[int] = None, subgrid_L: Optional[int] = None,
+              objs: Sequence[int] = (MDP_OBJ_TIME,), opts: Optional[MdpBuildOpts] = None,
+              stream=None) -> Model:
+    lib = load()
+    e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    h = P()
+    N = denv.env.N if N is None else N
+    L = denv.env.L if subgrid_L is None else subgrid_L
+    code = lib.mdp_build(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
+                         C.byref(opts) if opts is not None else None, _stream(stream), C.byref(h))
+    _check(code, "mdp_build")
+    return Model(h.value, denv.precision)
+
+
+def mdp_model_info(model: Model) -> MdpModelInfo:
+    info = MdpModelInfo()
+    _check(load().mdp_model_info(model.handle, C.byref(info)), "mdp_model_info")
+    return info
+
+
+def mdp_export_csr(model: Model, obj: int = 0, stream=None):
+    """Paper-layout CSR (row = a*|S| + s) as torch device tensors (rowptr, col, count, R)."""
+    import torch
+    info = mdp_model_info(model)
+    rows = info.rows
+    rowptr = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(max(info.nnz, 1), dtype=torch.int64, device="cuda")
+    cnt = torch.empty(max(info.nnz, 1), dtype=torch.int32, device="cuda")
+    R = torch.empty(rows, dtype=torch.float64 if model.precision else torch.float32, device="cuda")
+    _check(load().mdp_export_csr(model.handle, obj, _ptr(rowptr), _ptr(col), _ptr(cnt), _ptr(R),
+                                 _stream(stream)), "mdp_export_csr")
+    return rowptr, col[:info.nnz], cnt[:info.nnz], R
+
+
+def mdp_solve(model: Model, obj: int = 0, method: int = MDP_SOLVE_JACOBI, tol: float = 0.0,
+              max_sweeps: int = 0, V=None, policy=None, stream=None):
+    """Returns (V, policy, MdpSolveStats); V / policy are torch device tensors."""
+    import torch
+    info = mdp_model_info(model)
+    if V is None:
+        V = torch.empty(info.n_states + 1, dtype=torch.float64 if model.precision else torch.float32,
+                        device="cuda")
+    if policy is None:
+        policy = torch.empty(info.n_states, dtype=torch.int16, device="cuda")
+    st = MdpSolveStats()
+    _check(load().mdp_solve(model.handle, obj, method, float(tol), int(max_sweeps), _ptr(V),
+                            _ptr(policy), _stream(stream), C.byref(st)), "mdp_solve")
+    return V, policy, st
+
+
+def mdp_sample_coeffs(nt: int, N: int, K: int, sigma, seed: int, mdp_id: int = 0,
+                      precision: int = MDP_FP32, stream=None):
+    import torch
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    Y = torch.empty((nt, N, K), dtype=torch.float64 if precision else torch.float32, device="cuda")
+    _check(load().mdp_sample_coeffs(nt, N, K, sig.ctypes.data_as(P), seed, mdp_id, precision,
+                                    _ptr(Y), _stream(stream)), "mdp_sample_coeffs")
+    return Y
+
+
+def mdp_version() -> str:
+    return load().mdp_version().decode()
