@@ -1,0 +1,366 @@
+"""Benchmark: one step = the whole hot path on one synthetic workload.
+
+Default workload (N=1): the large single instance -- 200x200 grid, nt = 120,
+K = 8 DO modes, N = 5000 realizations, 32 actions, 21x21 sub-grid, all three
+objectives from one build -- i.e. one MDP build (coefficient sampling, fused
+transition counting and emit) followed by one Jacobi value iteration per
+objective, through the C ABI with every input resident in HBM.
+
+value = transitions sampled per second over the whole step (samples / step
+time); bellman_updates_per_s = (s, a) backups per second of the solve phase.
+With torchrun (N > 1) every rank builds and solves its own independent
+instance (different Philox key), no collective on the data path (weak scaling);
+the step time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the baseline arm: there is no
+reference implementation to install) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transitions sampled/s & Bellman updates/s (% HBM roofline); replan p50/p99 ms"
+UNIT = "transitions/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def workload(name, rank=0, nt=None):
+    from paper_2109_00857_gb300 import inputs
+    kw = {"mdp_id": rank}
+    if nt:
+        kw["nt"] = nt
+    env = getattr(inputs, name)(**kw)
+    return env
+
+
+def algorithmic_ops_per_sample(env):
+    """Issue-slot count the method itself needs per landing sample: 2 adds
+    (x + (v + a) dt in cell units, per coordinate), 2 floors (cell()), 1 bin
+    index, 1 count; plus the velocity synthesis 2K FMAs + 2 scalings per
+    (state, realization) shared by the A actions."""
+    return 6.0 + (2.0 * env.K + 2.0) / env.A
+
+
+def bellman_bytes_per_sweep(info, nS):
+    """Algorithmic bytes of one Jacobi sweep: 4 B per in-domain successor
+    (offset, count) and 4 B of R per row; per state the old V read, the V and
+    policy writes, the cell class, and one read of V(s') of the next layer
+    (the gathers are served from L1/L2).  Sink entries need no bytes (V = 0);
+    the sliced-ELL padding the layout carries is not counted."""
+    return 4 * info.nnz_domain + 4 * info.rows + nS * (4 + 4 + 2 + 1 + 4)
+
+
+class ClockSampler:
+    def __init__(self, idx):
+        self.idx = idx
+        self.f = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(env, seconds=12.0):
+    """The oracle as it stands, single thread, on a bounded sample of units
+    of the same workload (coefficients drawn first, not timed)."""
+    import oracle
+    Y = oracle.coeffs_for(env)
+    env_o = env
+    env_o.Y = Y
+    t_mid = env.nt // 2
+    u0 = t_mid * env.Nc + env.Nc // 3
+    per_unit = env.N * env.A
+    # calibrate on a few units, then size the sample to ~seconds
+    t0 = time.perf_counter()
+    oracle.build_units(env_o, env.objectives, u0, u0 + 4, with_literal=False)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = max(4, min(env.Nc, int(4 * seconds / dt)))
+    t0 = time.perf_counter()
+    out = oracle.build_units(env_o, env.objectives, u0, u0 + n, with_literal=False)
+    dt = time.perf_counter() - t0
+    env.Y = None
+    assert out["status"] == 0
+    return {"value": n * per_unit / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} (t, cell) units of layer t={t_mid} x {env.A} actions x N={env.N} "
+                      f"({n * per_unit:.3e} landings, {dt:.1f} s, FP64 oracle, 1 thread)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """Baseline arm: the FP64 oracle on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    env = workload(args.config)
+    import oracle
+    Y = oracle.coeffs_for(env)
+    env.Y = Y
+    t_mid = env.nt // 2
+    u0 = t_mid * env.Nc
+    per_unit = env.N * env.A
+    t0 = time.perf_counter()
+    oracle.build_units(env, env.objectives, u0, u0 + 2, with_literal=False)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, int(args.ref_step_seconds / max(per, 1e-6)))
+    for w in range(args.warmup):
+        oracle.build_units(env, env.objectives, u0, u0 + n, with_literal=False)
+    times = []
+    for k in range(args.steps):
+        a = u0 + (k * n) % max(1, env.Nc - n)
+        t0 = time.perf_counter()
+        oracle.build_units(env, env.objectives, a, a + n, with_literal=False)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    val = args.steps * n * per_unit / T
+    sample = (f"{n} (t, cell) units of layer t={t_mid} per step x {env.A} actions x N={env.N}; "
+              f"FP64 oracle build, 1 thread")
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": env.name, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="large", choices=["tiny", "energy", "large"])
+    ap.add_argument("--solve", default="jacobi", choices=["jacobi", "layered"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--nt", type=int, default=0, help="override nt (small profiling cases only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2109_00857_gb300 import mdp
+    mdp.load()
+
+    env = workload(args.config, rank, args.nt)
+    objs = env.objectives
+    method = mdp.MDP_SOLVE_JACOBI if args.solve == "jacobi" else mdp.MDP_SOLVE_LAYERED
+    denv = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    stream = torch.cuda.Stream()
+    Vbuf = [torch.empty(env.nS + 1, dtype=torch.float32, device="cuda") for _ in objs]
+    Pbuf = [torch.empty(env.nS, dtype=torch.int16, device="cuda") for _ in objs]
+    opts = mdp.MdpBuildOpts()
+    opts.threads, opts.chunk = args.threads, args.chunk
+    rec = {}
+
+    def step(d=denv):
+        m = mdp.mdp_build(d, objs=objs, opts=opts, stream=stream)
+        info = m.info()
+        sts = []
+        for o in range(len(objs)):
+            _, _, st = mdp.mdp_solve(m, o, method=method, tol=0.0, V=Vbuf[o], policy=Pbuf[o],
+                                     stream=stream)
+            sts.append(st)
+        rec["info"], rec["stats"] = info, sts
+        m.free()
+        return info, sts
+
+    for _ in range(args.warmup):
+        step()
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms, solve_ms, build_ms, samples, backups, launches, sweeps = [], [], [], 0, 0, 0, []
+    e0.record(stream)
+    for _ in range(args.steps):
+        info, sts = step()
+        kern_ms.append(info.kernel_ms)
+        build_ms.append(info.build_ms)
+        solve_ms.append(sum(s.solve_ms for s in sts))
+        samples += info.samples
+        backups += sum(s.backups for s in sts)
+        sweeps.append([s.sweeps for s in sts])
+        # Jacobi: nt + 1 sweep launches (those after convergence exit at once) + finalize;
+        # layered: one launch per time layer
+        launches += info.launches + sum((env.nt + 2) if method == 0 else env.nt for s in sts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    t_ms = e0.elapsed_time(e1)
+    tt = torch.tensor([t_ms, float(samples), float(backups)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = tt[0:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = tt[1:3].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        t_ms, samples, backups = float(tmax[0]), float(tsum[0]), float(tsum[1])
+    value = samples / (t_ms / 1e3)
+    info = rec["info"]
+    hbm, sm_mhz, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # build kernel (dominant) against the issue-slot roofline
+    ops = algorithmic_ops_per_sample(env)
+    kmean = statistics.mean(kern_ms)
+    build_achieved = info.samples * ops / (kmean / 1e3) / 1e12      # Tops/s
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12
+    # Bellman sweep against HBM
+    bpsw = bellman_bytes_per_sweep(info, env.nS)
+    nsw = sum(sum(x) for x in sweeps)
+    sweep_ms = sum(solve_ms) / max(1, nsw) if method == 0 else sum(solve_ms) / len(solve_ms) / len(objs)
+    bell_achieved = bpsw / (sweep_ms / 1e3) / 1e9
+    roof_build = {"kernel": "build_fp32_kernel", "bound": "alu", "achieved": build_achieved,
+                  "peak": alu_peak, "unit": "Tops/s", "frac": build_achieved / alu_peak,
+                  "traffic": None,
+                  "ops_per_sample": ops, "ms_per_launch": kmean,
+                  "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
+    roof_bell = {"kernel": "jacobi_kernel" if method == 0 else "layer_kernel", "bound": "hbm",
+                 "achieved": bell_achieved, "peak": hbm, "unit": "GB/s", "frac": bell_achieved / hbm,
+                 "traffic": None, "bytes_per_sweep": bpsw, "ms_per_sweep": sweep_ms,
+                 "peak_basis": f"hbm_gbs ({peak_kind})"}
+    build_share = sum(kern_ms) / t_ms
+    solve_share = sum(solve_ms) / t_ms
+    dominant = roof_build if build_share >= solve_share else roof_bell
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": env.name, "objectives": list(objs), "solve": args.solve,
+                       "tol": 0.0, "subgrid": env.L, "l2": "inputs_gt_l2 (model 7 GB, modes 307 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "bellman_updates_per_s": backups / (sum(solve_ms) / 1e3) / max(1, 1),
+            "build_transitions_per_s": info.samples / (statistics.mean(build_ms) / 1e3),
+            "phase_ms": {"build": statistics.mean(build_ms), "build_kernel": kmean,
+                         "solve": statistics.mean(solve_ms)},
+            "sweeps": sweeps[-1],
+            "roofline": dominant, "roofline_build": roof_build, "roofline_bellman": roof_bell,
+            "gpu_launches": launches, "clocks": clocks,
+            "model": {"nnz": info.nnz, "rows": info.rows, "max_row_nnz": info.max_row_nnz,
+                      "device_bytes": info.device_bytes}}
+    if world > 1:
+        line["bellman_updates_per_s"] = backups / (t_ms / 1e3)
+
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        host = {k: getattr(denv, k).cpu().pin_memory() for k in ("vbar", "modes", "gbar", "obstacle", "target")
+                if getattr(denv, k) is not None}
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        Vh = [torch.empty_like(v, device="cpu").pin_memory() for v in Vbuf]
+        Ph = [torch.empty_like(p, device="cpu").pin_memory() for p in Pbuf]
+        d2h = sum(v.numel() * 4 for v in Vh) + sum(p.numel() * 2 for p in Ph)
+        for _ in range(max(1, args.warmup)):
+            with torch.cuda.stream(stream):
+                for k, t in host.items():
+                    getattr(denv, k).copy_(t, non_blocking=True)
+            step()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                for k, t in host.items():
+                    getattr(denv, k).copy_(t, non_blocking=True)
+            step()
+            with torch.cuda.stream(stream):
+                for v, vh in zip(Vbuf, Vh):
+                    vh.copy_(v, non_blocking=True)
+                for p, ph in zip(Pbuf, Ph):
+                    ph.copy_(p, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        if world > 1:
+            tm = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tm[0])
+        line["e2e"] = {"value": samples / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+                       "wall_s": time.perf_counter() - t0}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(workload(args.config, rank, args.nt), args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

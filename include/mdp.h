@@ -114,6 +114,9 @@ typedef struct {
   int32_t no_compact;      /* 1: keep the worst-case entry pool instead of compacting it */
   int32_t threads;         /* build CTA size for FP32 (multiple of 64); 0 = autotuned */
   int32_t chunk;           /* realizations staged per pass; 0 = autotuned */
+  int32_t hist_cap;        /* per-row histogram bins of the warp-per-slice kernel; 0 = 64;
+                              slices wider than this go to the full-window kernel
+                              (1 sends every sampled slice there) */
 } mdp_build_opts;
 
 typedef struct mdp_model_t *mdp_model;
@@ -145,7 +148,11 @@ typedef struct {
   int64_t pool_columns;    /* 32-entry columns of the sliced-ELL entry pool in use */
   int64_t device_bytes;    /* device memory owned by the model */
   int64_t samples;         /* landing evaluations performed (N per sampled (s,a)) */
-  double build_ms;         /* device time of the build kernels (CUDA events) */
+  double build_ms;         /* device time of sampler + build kernels (CUDA events) */
+  double kernel_ms;        /* device time of the fused build kernel alone (CUDA events) */
+  int32_t launches;        /* kernels the build launched */
+  int64_t wide_slices;     /* slices built by the full-window kernel (histogram > hist_cap) */
+  int64_t nnz_domain;      /* stored successors inside the domain (sink entries excluded) */
 } mdp_model_info_t;
 
 mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *out);

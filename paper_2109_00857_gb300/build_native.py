@@ -24,6 +24,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "api.cu": [],
     "build_fp32.cu": [],
+    "build_warp.cu": [],
     "bellman.cu": [],
     "serve.cu": [],
     "check_fp64.cu": ["-fmad=false"],

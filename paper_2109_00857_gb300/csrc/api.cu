@@ -123,7 +123,9 @@ struct Pinned {
 static void free_model_memory(mdp_model_t *m, cudaStream_t st) {
   dev_free(m->pool, st);
   dev_free(m->slice_off, st);
+  dev_free(m->slice_w, st);
   dev_free(m->nnz, st);
+  dev_free(m->sinkc, st);
   dev_free(m->R, st);
   dev_free(m->cls, st);
   dev_free(m->delta, st);
@@ -132,7 +134,9 @@ static void free_model_memory(mdp_model_t *m, cudaStream_t st) {
   dev_free(m->solve_stats_d, st);
   m->pool = nullptr;
   m->slice_off = nullptr;
+  m->slice_w = nullptr;
   m->nnz = nullptr;
+  m->sinkc = nullptr;
   m->R = nullptr;
   m->cls = nullptr;
   m->delta = nullptr;
@@ -246,10 +250,12 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   double *sig_d = nullptr;
   TRY(dev_alloc((void **)&m->cnt, sizeof(unsigned long long) * CNT_N, st));
   TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
-  cudaEvent_t ev0, ev1;
+  cudaEvent_t ev0, ev1, evk;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
+  cudaEventCreate(&evk);
   cudaEventRecord(ev0, st);
+  int launches = 0;
   if (!Y && env->K > 0) {
     TRY(dev_alloc(&Yown, fsz * (size_t)grid->nt * N * env->K, st));
     TRY(dev_alloc((void **)&sig_d, sizeof(double) * env->K, st));
@@ -258,6 +264,7 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
                              prec == MDP_FP64_CHECK ? (double *)Yown : nullptr,
                              prec == MDP_FP32 ? (float *)Yown : nullptr, m->cnt + CNT_CAPPED, st));
     Y = Yown;
+    ++launches;
   }
 
   // -- sub-grid side: given, or from the component-wise field extremes (Sec. III-B)
@@ -269,9 +276,11 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
     TRY(dev_alloc((void **)&ex, sizeof(unsigned int) * nex, st));
     TRY(cudaMemsetAsync(ex, 0, sizeof(unsigned int) * nex, st));
     TRY(launch_absmax(env->vbar, prec, nS * 2, 1, 1, 2, ex, st));
+    ++launches;
     if (K > 0) {
       TRY(launch_absmax(env->modes, prec, nS * K * 2, K, Nc, 2, ex + 2, st));
       TRY(launch_absmax(Y, prec, (int64_t)grid->nt * N * K, K, 1, 1, ex + 2 + 2 * K, st));
+      launches += 2;
     }
     std::vector<unsigned int> hx(nex);
     TRY(cudaMemcpyAsync(hx.data(), ex, sizeof(unsigned int) * nex, cudaMemcpyDeviceToHost, st));
@@ -298,22 +307,34 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   m->L = L;
   m->h = (L - 1) / 2;
   m->nbins = L * L;
+  // successors are stored as signed 16-bit offsets dj*Nx + di
+  if ((int64_t)m->h * (grid->nx + 1) > 32767)
+    return fail(arg_fail("sub-grid half-width * (nx + 1) must be <= 32767 (16-bit successor offsets)"));
 
-  // -- model memory
+  // -- model memory.  The entry pool is sized for an average slice width of
+  // kPoolGuess columns first; if the build runs out of columns it is rebuilt
+  // once with the worst case (every slice row_cap wide).
   const int Wmax = std::min(row_cap, m->nbins + 1);
-  uint64_t cap_cols = (uint64_t)m->n_slices * (uint64_t)Wmax;
+  const int kPoolGuess = 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const uint64_t budget_cols = (uint64_t)(0.6 * (double)free_b) / 128;
-  if (cap_cols > budget_cols) cap_cols = budget_cols;
-  if (cap_cols < 1) cap_cols = 1;
+  auto pool_cols_for = [&](int width) {
+    uint64_t c = (uint64_t)m->n_slices * (uint64_t)std::min(width, Wmax) + 64;
+    if (c > budget_cols) c = budget_cols;
+    return c < 1 ? (uint64_t)1 : c;
+  };
+  uint64_t cap_cols = pool_cols_for(kPoolGuess);
   TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
   TRY(dev_alloc((void **)&m->slice_off, sizeof(uint32_t) * (size_t)m->n_slices, st));
+  TRY(dev_alloc((void **)&m->slice_w, (size_t)m->n_slices, st));
   TRY(dev_alloc((void **)&m->nnz, (size_t)m->rows_pad, st));
+  TRY(dev_alloc((void **)&m->sinkc, sizeof(uint16_t) * (size_t)m->rows_pad, st));
   TRY(dev_alloc(&m->R, fsz * (size_t)m->rows_pad * n_obj, st));
   TRY(dev_alloc((void **)&m->cls, (size_t)nS, st));
   TRY(dev_alloc((void **)&m->delta, sizeof(int32_t) * (size_t)m->nbins, st));
   TRY(launch_prepare(env->obstacle, env->target, m->cls, grid->nx, grid->ny, grid->nt, m->delta, L, st));
+  ++launches;
 
   BuildArgs ba;
   memset(&ba, 0, sizeof(ba));
@@ -323,7 +344,7 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   ba.lam = (float)lam;
   ba.vbar = env->vbar; ba.modes = env->modes; ba.Y = Y; ba.gbar = env->gbar; ba.cls = m->cls;
   ba.act = at; ba.rw = rw;
-  ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.nnz = m->nnz;
+  ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.slice_w = m->slice_w; ba.nnz = m->nnz; ba.sinkc = m->sinkc;
   ba.R = m->R; ba.cnt = m->cnt;
   ba.slice_begin = 0; ba.slice_end = m->n_slices;
   int threads = (opts && opts->threads > 0) ? opts->threads : 256;
@@ -331,24 +352,56 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   int chunk = (opts && opts->chunk > 0) ? opts->chunk : 1024;
   if (chunk > N) chunk = N;
   ba.chunk = chunk;
-  if (prec == MDP_FP64_CHECK) {
-    TRY(launch_build_fp64(ba, st));
-  } else {
-    TRY(launch_build_fp32(ba, threads, num_sms(), st));
-  }
-  cudaEventRecord(ev1, st);
+  int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : 64;
+  if (hist_cap > 4096) return fail(arg_fail("hist_cap must be <= 4096"));
+  uint32_t *defer = nullptr;
+  if (prec == MDP_FP32) TRY(dev_alloc((void **)&defer, sizeof(uint32_t) * (size_t)m->n_slices, st));
+  ba.cap_bins = hist_cap;
+  ba.defer = defer;
+  ba.defer_in = nullptr;
   static thread_local Pinned pin;
   if (!pin.p) return fail(cuda_fail(cudaErrorMemoryAllocation, "cudaMallocHost"));
-  TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+  const unsigned long long *c = pin.p;
+  for (int attempt = 0;; ++attempt) {
+    cudaEventRecord(evk, st);
+    if (prec == MDP_FP64_CHECK) {
+      TRY(launch_build_fp64(ba, st));
+      ++launches;
+    } else {
+      // warp-per-slice kernel, then the full-window CTA kernel over what it deferred
+      TRY(launch_build_warp(ba, 8, num_sms(), st));
+      BuildArgs bd = ba;
+      bd.defer_in = defer;
+      TRY(launch_build_fp32(bd, threads, num_sms(), st));
+      launches += 2;
+    }
+    cudaEventRecord(ev1, st);
+    TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    const uint64_t worst = pool_cols_for(Wmax);
+    if (c[CNT_POOL_FULL] == 0 || attempt > 0 || worst <= cap_cols) break;
+    // rebuild once with the worst-case pool (counters reset, sampled Y kept)
+    dev_free(m->pool, st);
+    cap_cols = worst;
+    TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+    TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_CAPPED, st));
+    TRY(cudaMemsetAsync(m->cnt + CNT_WORK, 0, sizeof(unsigned long long) * (CNT_N - CNT_WORK), st));
+    ba.pool = m->pool;
+    ba.pool_cap_cols = cap_cols;
+  }
   if (Yown) dev_free(Yown, st);
   if (sig_d) dev_free(sig_d, st);
-  TRY(cudaStreamSynchronize(st));
-  float ms = 0.f;
+  if (defer) dev_free(defer, st);
+  m->deferred = (int64_t)c[CNT_DEFER_N];
+  float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventElapsedTime(&kms, evk, ev1);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  cudaEventDestroy(evk);
   m->build_ms = ms;
-  const unsigned long long *c = pin.p;
+  m->kernel_ms = kms;
+  m->launches = launches;
   if (c[CNT_OVERFLOW]) {
     char buf[256];
     snprintf(buf, sizeof buf, "%llu landing(s)/row(s) left the %dx%d neighbouring sub-grid; use a larger subgrid_L",
@@ -368,6 +421,7 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   }
   m->pool_cols = c[CNT_POOL_COLS];
   m->nnz_total = (int64_t)c[CNT_NNZ];
+  m->nnz_domain = (int64_t)c[CNT_DOMAIN];
   m->max_row_nnz = (int32_t)c[CNT_MAXROW];
   m->samples = (int64_t)c[CNT_SAMPLES];
   // -- compaction: the bump-allocated columns are contiguous, so shrink the pool
@@ -379,7 +433,7 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
     m->pool = np;
     cap_cols = std::max<uint64_t>(m->pool_cols, 1);
   }
-  m->device_bytes = (int64_t)cap_cols * 128 + 4 * m->n_slices + m->rows_pad + (int64_t)fsz * m->rows_pad * n_obj +
+  m->device_bytes = (int64_t)cap_cols * 128 + 5 * m->n_slices + 3 * m->rows_pad + (int64_t)fsz * m->rows_pad * n_obj +
                     nS + 4 * m->nbins + 8 * CNT_N;
   *out = m;
 #undef TRY
@@ -403,6 +457,10 @@ extern "C" mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *o) {
   o->device_bytes = m->device_bytes + (m->Vtmp ? (int64_t)(m->nS + 1) * (m->precision ? 8 : 4) : 0);
   o->samples = m->samples;
   o->build_ms = m->build_ms;
+  o->kernel_ms = m->kernel_ms;
+  o->launches = m->launches;
+  o->wide_slices = m->deferred;
+  o->nnz_domain = m->nnz_domain;
   return MDP_OK;
 }
 
@@ -428,6 +486,13 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
   cudaStream_t st = (cudaStream_t)stream;
   const size_t fsz = m->precision == MDP_FP64_CHECK ? 8 : 4;
   const size_t vbytes = fsz * (size_t)(m->nS + 1);
+  // the solver streams slices with 16-byte-aligned bulk copies and indexes
+  // successors with 32-bit offsets
+  if ((((uintptr_t)m->pool) | ((uintptr_t)m->R) | ((uintptr_t)m->nnz)) & 15) {
+    set_error("model arrays are not 16-byte aligned");
+    return MDP_ERR_CUDA;
+  }
+  if (m->nS + m->Nc >= ((int64_t)1 << 31)) return arg_fail("more than 2^31 states is not supported by the solver");
   if (method == MDP_SOLVE_JACOBI && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
   double *sd = nullptr;
   MDP_CUDA_TRY(dev_alloc((void **)&sd, sizeof(double) * (4 + (size_t)max_sweeps), st));
@@ -435,11 +500,13 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
   MDP_CUDA_TRY(cudaMemsetAsync(V, 0, vbytes, st));
   if (method == MDP_SOLVE_JACOBI) MDP_CUDA_TRY(cudaMemsetAsync(m->Vtmp, 0, vbytes, st));
   SolveArgs a;
-  a.pool = m->pool; a.slice_off = m->slice_off; a.nnz = m->nnz;
+  a.pool = m->pool; a.slice_off = m->slice_off; a.slice_w = m->slice_w; a.nnz = m->nnz;
+  a.wcap = std::max(1, m->max_row_nnz);
   a.R = static_cast<const char *>(m->R) + fsz * (size_t)obj * m->rows_pad;
   a.cls = m->cls; a.delta = m->delta;
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;
-  a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.tol = tol;
+  a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
+  a.err = reinterpret_cast<int *>(sd + 2);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -449,7 +516,8 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
   else ce = launch_layered(a, m->precision, m->nt, V, policy, sd, st);
   cudaEventRecord(e1, st);
   double hs[2] = {0, 0};
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hs, sd, sizeof(hs), cudaMemcpyDeviceToHost, st);
+  double hs3[3] = {0, 0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hs3, sd, sizeof(hs3), cudaMemcpyDeviceToHost, st);
   dev_free(sd, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   float ms = 0.f;
@@ -457,6 +525,14 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (ce != cudaSuccess) return cuda_fail(ce, "mdp_solve");
+  hs[0] = hs3[0];
+  hs[1] = hs3[1];
+  int errw = 0;
+  memcpy(&errw, &hs3[2], sizeof(int));
+  if (errw) {
+    set_error("a bounded device wait expired in the Bellman pipeline");
+    return MDP_ERR_TIMEOUT;
+  }
   if (stats) {
     if (method == MDP_SOLVE_JACOBI) {
       stats->sweeps = (int32_t)hs[0];

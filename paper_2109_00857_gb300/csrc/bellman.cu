@@ -89,79 +89,204 @@ struct Acc<double> {
   __device__ __forceinline__ double q(double R, double) const { return __dadd_rn(R, v); }
 };
 
-// One warp per slice in [sl_lo, sl_hi).  Writes Vout[s] and policy[s] for
-// states in [s_lo, s_hi); returns the warp's residual contribution.
-template <typename RT>
-__device__ __forceinline__ double backup_slice(const SolveArgs &a, int64_t sl, int64_t s_lo,
-                                              int64_t s_hi, const RT *Vin, RT *Vout,
-                                              int16_t *__restrict__ policy) {
-  const int lane = threadIdx.x & 31;
-  const int q = lane / a.A_pad, act = lane % a.A_pad;
-  const int64_t s = sl * a.spw + q;
-  const bool valid = s >= s_lo && s < s_hi && act < a.A;
-  const int64_t ir = sl * 32 + lane;
-  const uint32_t off = __ldg(a.slice_off + sl);
-  const int e = valid ? (int)__ldg(a.nnz + ir) : 0;
-  Acc<RT> acc;
-  const int64_t nxt = s + a.Nc;
-  const uint32_t *col = a.pool + (size_t)off * 32 + lane;
-  for (int k = 0; k < e; ++k) {
-    const uint32_t w = __ldcs(col + (size_t)k * 32);
-    const uint32_t b = w & 0xFFFFu;
-    const int64_t sp = (b == kSinkBin) ? a.nS : nxt + __ldg(a.delta + b);
-    acc.add(w >> 16, Vin[sp], a.N);
+// ---- mbarrier / bulk-copy helpers (PTX) ----
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2 s of clock cycles so a lost arrival can
+// never hang the GPU; the caller reports the timeout through the error word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;
   }
-  RT qv;
-  if (valid) qv = acc.q(__ldcs(static_cast<const RT *>(a.R) + ir), (RT)1 / (RT)a.N);
-  else qv = -(RT)INFINITY;
-  int qa = act;
-  for (int o = 1; o < a.A_pad; o <<= 1) {
-    const RT oq = __shfl_xor_sync(0xffffffffu, qv, o);
-    const int oa = __shfl_xor_sync(0xffffffffu, qa, o);
-    if (oq > qv || (oq == qv && oa < qa)) {
-      qv = oq;
-      qa = oa;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+constexpr int kWarps = 8;     // warps per CTA
+constexpr int kDepth = 3;     // slices each warp keeps in flight
+
+struct PipeRange {
+  int64_t sl_lo, sl_hi;   // slices of this launch
+  int64_t s_lo, s_hi;     // states whose V this launch writes
+  int stage_bytes;        // bytes per stage
+  int dtab_smem;          // 1: delta table staged in shared memory
+};
+
+static int stage_bytes_for(int wcap, size_t rsz) {
+  int b = wcap * 128 + 32 * (int)rsz;
+  return (b + 127) & ~127;
+}
+
+// A CTA streams a contiguous block of slices (so its V(s') gathers stay in a
+// small window of layer t+1 that L1 keeps); warp w takes slices w, w+8, ...
+// and keeps kDepth of them in flight in private stages: lane 0 copies a
+// slice's entry columns, its 32 R values and its 32 row lengths with
+// cp.async.bulk (TMA) into a stage whose mbarrier counts the bytes, while the
+// warp works on an earlier stage: gathers V(s'), forms Q, reduces max/argmax
+// over each state's A_pad lanes and writes V and the policy.  Slice offsets
+// and widths of the next 32 slices are read in one coalesced load.
+// res != nullptr: Jacobi sweep k (exits at once if sweep k-1 met the
+// tolerance) with the residual reduced into res[k-1].
+template <typename RT>
+__global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, const RT *Vin, RT *Vout,
+                                                              int16_t *policy, unsigned long long *res, int k,
+                                                              PipeRange pr) {
+  if (res && k > 1 && __longlong_as_double((long long)res[k - 2]) <= a.tol) return;
+  if (*(volatile int *)a.err) return;   // an earlier launch of this solve timed out
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWarps];
+  __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // [kWarps][kDepth]
+  unsigned char *ring = sm + 256;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const int64_t total = pr.sl_hi - pr.sl_lo;
+  const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
+  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
+  const int64_t n_local = b_hi - b_lo;
+  if (n_local <= 0) return;
+
+  if (tid < kWarps * kDepth) mbar_init(smem_u32(full + tid), 1);
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  const size_t rsz = sizeof(RT);
+  const int roff = a.wcap * 128;          // R block offset inside a stage
+  unsigned char *myring = ring + (size_t)warp * kDepth * pr.stage_bytes;
+  uint64_t *myfull = full + warp * kDepth;
+
+  // 32-bit slice/state indices (the host guarantees |S| + Nc < 2^31)
+  const int n_mine = (n_local > warp) ? (int)((n_local - warp + kWarps - 1) / kWarps) : 0;
+  const int sl0 = (int)b_lo + warp;                       // my j-th slice: sl0 + j*kWarps
+  const uint32_t ring0 = smem_u32(myring), bar0 = smem_u32(myfull);
+  const RT *Rg = static_cast<const RT *>(a.R);
+  uint32_t m_off = 0, m_w = 0;   // lane l: metadata of my slice 32*(j/32) + l
+
+  // issue(j): copy my j-th slice into stage j % kDepth (whole warp calls it)
+  auto issue = [&](int j) {
+    if ((j & 31) == 0) {
+      const int jj = j + lane;
+      if (jj < n_mine) {
+        const int sl = sl0 + jj * kWarps;
+        m_off = __ldg(a.slice_off + sl);
+        m_w = __ldg(a.slice_w + sl);
+      }
+    }
+    const uint32_t off = __shfl_sync(0xffffffffu, m_off, j & 31);
+    const uint32_t W = __shfl_sync(0xffffffffu, m_w, j & 31);
+    if (lane == 0) {
+      const int st = j % kDepth;
+      wst_s[warp * kDepth + st] = (int)W;
+      const uint32_t sbase = ring0 + (uint32_t)(st * pr.stage_bytes);
+      const uint32_t fb = bar0 + 8u * (uint32_t)st;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage
+      mbar_expect_tx(fb, W * 128u + 32u * (uint32_t)rsz);
+      if (W) bulk_g2s(sbase, a.pool + (size_t)off * 32, W * 128u, fb);
+      bulk_g2s(sbase + (uint32_t)roff, Rg + (size_t)(sl0 + j * kWarps) * 32, 32u * (uint32_t)rsz, fb);
+    }
+    __syncwarp();
+  };
+
+  const int q = lane / a.A_pad, act = lane % a.A_pad;
+  const int nS = (int)a.nS, Nc = (int)a.Nc;
+  const int s_lo = (int)pr.s_lo, s_hi = (int)pr.s_hi;
+  const RT invN = (RT)1 / (RT)a.N;
+  float rf = 0.f;      // FP32 residual
+  double r = 0.0;      // FP64 residual
+  for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j);
+  int st = 0;
+  uint32_t phase = 0;
+  for (int j = 0; j < n_mine; ++j) {
+    if (!mbar_wait(bar0 + 8u * (uint32_t)st, phase)) {
+      if (lane == 0) atomicOr(a.err, 1);
+      // drain: wait (bounded) for the copies still in flight into my stages
+      for (int jj = j + 1; jj < j + kDepth && jj < n_mine; ++jj)
+        mbar_wait(bar0 + 8u * (uint32_t)(jj % kDepth), (uint32_t)(jj / kDepth) & 1);
+      break;
+    }
+    const unsigned char *sb = myring + st * pr.stage_bytes;
+    const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb) + lane;
+    const int s = (sl0 + j * kWarps) * a.spw + q;
+    const bool valid = s >= s_lo && s < s_hi && act < a.A;
+    const RT Rv = reinterpret_cast<const RT *>(sb + roff)[lane];
+    const int W = wst_s[warp * kDepth + st];
+    Acc<RT> acc;
+    // successor layer base of this state; rows without successors (last
+    // layer, padding lanes) hold only padding words and read V[|S|] = 0
+    const RT *Vn = Vin + ((s + Nc <= nS) ? s + Nc : nS);
+#pragma unroll 4
+    for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
+      const uint32_t w = ent[kk * 32];
+      acc.add(w >> 16, Vn[(int)(int16_t)(w & 0xFFFFu)], a.N);
+    }
+    __syncwarp();
+    if (j + kDepth < n_mine) issue(j + kDepth);   // refill the stage just read
+    if (++st == kDepth) {
+      st = 0;
+      phase ^= 1u;
+    }
+    RT qv = valid ? acc.q(Rv, invN) : -(RT)INFINITY;
+    int qa = act;
+    if (sizeof(RT) == 4 && a.A_pad == 32) {
+      // one state per warp: order-preserving integer key, warp max in one
+      // redux, lowest lane (= lowest action) among the maxima by ballot
+      const uint32_t bits = __float_as_uint((float)qv + 0.0f);   // -0 keys like +0
+      const uint32_t key = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+      const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+      qa = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
+      qv = __shfl_sync(0xffffffffu, qv, qa);
+    } else {
+      for (int o = 1; o < a.A_pad; o <<= 1) {
+        const RT oq = __shfl_xor_sync(0xffffffffu, qv, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, qa, o);
+        if (oq > qv || (oq == qv && oa < qa)) {
+          qv = oq;
+          qa = oa;
+        }
+      }
+    }
+    if (act == 0 && s >= s_lo && s < s_hi) {
+      const RT old = Vin[s];
+      Vout[s] = qv;
+      policy[s] = (__ldg(a.cls + s) != CLS_FREE) ? (int16_t)-1 : (int16_t)qa;
+      if constexpr (sizeof(RT) == 4) rf = fmaxf(rf, fabsf(qv - old));
+      else r = fmax(r, fabs(qv - old));
     }
   }
-  double res = 0.0;
-  if (act == 0 && s >= s_lo && s < s_hi) {
-    const RT old = Vin[s];
-    Vout[s] = qv;
-    policy[s] = (a.cls[s] != CLS_FREE) ? (int16_t)-1 : (int16_t)qa;
-    res = fabs((double)qv - (double)old);
+  if constexpr (sizeof(RT) == 4) r = (double)rf;
+  if (res) {
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) wmax[warp] = r;
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int i = 0; i < kWarps; ++i) m = fmax(m, wmax[i]);
+      if (m > 0.0) atomicMax(&res[k - 1], (unsigned long long)__double_as_longlong(m));
+    }
   }
-  return res;
-}
-
-// Jacobi sweep k (1-based) reads V_{k-1} and writes V_k.  res[k-1] holds the
-// residual of sweep k (bits of a non-negative double), zero-initialised.
-template <typename RT>
-__global__ void __launch_bounds__(256) jacobi_kernel(SolveArgs a, const RT *Vin, RT *Vout,
-                                                     int16_t *policy,
-                                                     unsigned long long *res, int k) {
-  if (k > 1 && __longlong_as_double((long long)res[k - 2]) <= a.tol) return;  // converged earlier
-  __shared__ double wmax[8];
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double r = 0.0;
-  for (int64_t sl = gw; sl < a.n_slices; sl += nw) r = fmax(r, backup_slice<RT>(a, sl, 0, a.nS, Vin, Vout, policy));
-  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, wmax[i]);
-    if (m > 0.0) atomicMax(&res[k - 1], (unsigned long long)__double_as_longlong(m));
-  }
-}
-
-// Backward layer t: V of layer t+1 is final, so one pass per layer suffices.
-template <typename RT>
-__global__ void __launch_bounds__(256) layer_kernel(SolveArgs a, RT *V, int16_t *policy, int64_t s_lo,
-                                                    int64_t s_hi, int64_t sl_lo, int64_t sl_hi) {
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = sl_lo + gw; sl < sl_hi; sl += nw) backup_slice<RT>(a, sl, s_lo, s_hi, V, V, policy);
 }
 
 // stats_d[0] = sweeps, [1] = residual of the last sweep.  Copies the final
@@ -186,13 +311,24 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
     Va[i] = Vb[i];
 }
 
-static int solve_blocks(int64_t slices) {
-  int64_t warps = slices;
-  int64_t blocks = (warps + 7) / 8;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  return (int)blocks;
+template <typename RT>
+static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
+  pr->stage_bytes = stage_bytes_for(a.wcap, sizeof(RT));
+  pr->dtab_smem = 0;
+  *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
+  if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(bellman_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<RT>, 32 * kWarps, *smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t b = (int64_t)num_sms() * per_sm;
+  const int64_t want = (slices + 4 * kWarps - 1) / (4 * kWarps);   // >= 4 slices per warp
+  if (b > want) b = want;
+  if (b < 1) b = 1;
+  *blocks = (int)b;
+  return cudaSuccess;
 }
 
 template <typename RT>
@@ -202,11 +338,19 @@ static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, RT *Va, RT *Vb, 
   unsigned long long *res = reinterpret_cast<unsigned long long *>(stats_d + 4);
   cudaError_t e = cudaMemsetAsync(res, 0, sizeof(unsigned long long) * (size_t)max_sweeps, st);
   if (e != cudaSuccess) return e;
-  const int blocks = solve_blocks(a.n_slices);
+  PipeRange pr;
+  size_t smem = 0;
+  int blocks = 1;
+  e = pipe_config<RT>(a, a.n_slices, &pr, &smem, &blocks);
+  if (e != cudaSuccess) return e;
+  pr.sl_lo = 0;
+  pr.sl_hi = a.n_slices;
+  pr.s_lo = 0;
+  pr.s_hi = a.nS;
   for (int k = 1; k <= max_sweeps; ++k) {
     const RT *vin = (k & 1) ? Va : Vb;
     RT *vout = (k & 1) ? Vb : Va;
-    jacobi_kernel<RT><<<blocks, 256, 0, st>>>(a, vin, vout, policy, res, k);
+    bellman_kernel<RT><<<blocks, 32 * kWarps, smem, st>>>(a, vin, vout, policy, res, k, pr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -226,9 +370,16 @@ cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, voi
 template <typename RT>
 static cudaError_t layered_t(const SolveArgs &a, int nt, RT *V, int16_t *policy, cudaStream_t st) {
   for (int t = nt - 1; t >= 0; --t) {
-    const int64_t s_lo = (int64_t)t * a.Nc, s_hi = s_lo + a.Nc;
-    const int64_t sl_lo = s_lo / a.spw, sl_hi = (s_hi + a.spw - 1) / a.spw;
-    layer_kernel<RT><<<solve_blocks(sl_hi - sl_lo), 256, 0, st>>>(a, V, policy, s_lo, s_hi, sl_lo, sl_hi);
+    PipeRange pr;
+    pr.s_lo = (int64_t)t * a.Nc;
+    pr.s_hi = pr.s_lo + a.Nc;
+    pr.sl_lo = pr.s_lo / a.spw;
+    pr.sl_hi = (pr.s_hi + a.spw - 1) / a.spw;
+    size_t smem = 0;
+    int blocks = 1;
+    cudaError_t e = pipe_config<RT>(a, pr.sl_hi - pr.sl_lo, &pr, &smem, &blocks);
+    if (e != cudaSuccess) return e;
+    bellman_kernel<RT><<<blocks, 32 * kWarps, smem, st>>>(a, V, V, policy, nullptr, 0, pr);
   }
   return cudaGetLastError();
 }
@@ -242,12 +393,13 @@ cudaError_t launch_layered(const SolveArgs &a, int precision, int nt, void *V, i
 
 // -------------------------------------------------------------- export ----
 // Paper layout row r = a*|S| + s.
-__global__ void export_count_kernel(const uint8_t *__restrict__ nnz, int64_t nS, int A, int A_pad,
-                                    int64_t *__restrict__ rowlen) {
+__global__ void export_count_kernel(const uint8_t *__restrict__ nnz, const uint16_t *__restrict__ sinkc,
+                                    int64_t nS, int A, int A_pad, int64_t *__restrict__ rowlen) {
   const int64_t rows = nS * A;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t act = r / nS, s = r % nS;
-    rowlen[r] = nnz[s * A_pad + act];
+    const int64_t ir = s * A_pad + act;
+    rowlen[r] = nnz[ir] + (sinkc[ir] ? 1 : 0);
   }
 }
 
@@ -296,9 +448,9 @@ static cudaError_t exclusive_scan(int64_t *x, int64_t n, int64_t *scratch, cudaS
 
 template <typename RT>
 __global__ void export_fill_kernel(const uint32_t *__restrict__ pool, const uint32_t *__restrict__ slice_off,
-                                   const uint8_t *__restrict__ nnz, const RT *__restrict__ Rsrc,
-                                   const int32_t *__restrict__ delta, int64_t nS, int64_t Nc, int A,
-                                   int A_pad, int spw, int64_t n_slices, const int64_t *__restrict__ rowptr,
+                                   const uint8_t *__restrict__ nnz, const uint16_t *__restrict__ sinkc,
+                                   const RT *__restrict__ Rsrc, int64_t nS, int64_t Nc, int A, int A_pad,
+                                   int spw, int64_t n_slices, const int64_t *__restrict__ rowptr,
                                    int64_t *col, int32_t *count, RT *Rdst) {
   const int64_t nrow = n_slices * 32;
   for (int64_t ir = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ir < nrow; ir += (int64_t)gridDim.x * blockDim.x) {
@@ -309,15 +461,20 @@ __global__ void export_fill_kernel(const uint32_t *__restrict__ pool, const uint
     if (s >= nS || act >= A) continue;
     const int64_t r = (int64_t)act * nS + s;
     if (Rdst) Rdst[r] = Rsrc[ir];
+    if (!col && !count) continue;
     const int e = nnz[ir];
-    if (e == 0 || (!col && !count)) continue;
-    const uint32_t off = slice_off[sl];
     const int64_t o = rowptr[r];
-    for (int k = 0; k < e; ++k) {
-      const uint32_t w = pool[((size_t)off + k) * 32 + lane];
-      const uint32_t b = w & 0xFFFFu;
-      if (col) col[o + k] = (b == kSinkBin) ? nS : s + Nc + delta[b];
-      if (count) count[o + k] = (int32_t)(w >> 16);
+    if (e > 0) {
+      const uint32_t off = slice_off[sl];
+      for (int k = 0; k < e; ++k) {
+        const uint32_t w = pool[((size_t)off + k) * 32 + lane];
+        if (col) col[o + k] = s + Nc + (int64_t)(int16_t)(w & 0xFFFFu);
+        if (count) count[o + k] = (int32_t)(w >> 16);
+      }
+    }
+    if (sinkc[ir]) {
+      if (col) col[o + e] = nS;
+      if (count) count[o + e] = (int32_t)sinkc[ir];
     }
   }
 }
@@ -328,7 +485,7 @@ cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_
   int64_t blocks = (rows + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  export_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(m->nnz, m->nS, m->A, m->A_pad, rowptr);
+  export_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(m->nnz, m->sinkc, m->nS, m->A, m->A_pad, rowptr);
   cudaError_t e = cudaMemsetAsync(rowptr + rows, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return e;
   // scan scratch: geometric series of tile counts
@@ -345,12 +502,12 @@ cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_
   const size_t esz = (m->precision == MDP_FP64_CHECK) ? 8 : 4;
   if (m->precision == MDP_FP64_CHECK)
     export_fill_kernel<double><<<(unsigned)fb, 256, 0, st>>>(
-        m->pool, m->slice_off, m->nnz, static_cast<const double *>(m->R) + (size_t)obj * m->rows_pad,
-        m->delta, m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (double *)R);
+        m->pool, m->slice_off, m->nnz, m->sinkc, static_cast<const double *>(m->R) + (size_t)obj * m->rows_pad,
+        m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (double *)R);
   else
     export_fill_kernel<float><<<(unsigned)fb, 256, 0, st>>>(
-        m->pool, m->slice_off, m->nnz, static_cast<const float *>(m->R) + (size_t)obj * m->rows_pad,
-        m->delta, m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (float *)R);
+        m->pool, m->slice_off, m->nnz, m->sinkc, static_cast<const float *>(m->R) + (size_t)obj * m->rows_pad,
+        m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (float *)R);
   (void)esz;
   e = cudaGetLastError();
   dev_free(scratch, st);

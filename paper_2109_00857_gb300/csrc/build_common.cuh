@@ -70,11 +70,19 @@ __device__ __forceinline__ RT load_field(const void *p, int64_t i) {
 }
 
 // ------------------------------------------------------------------ emit --
+// Entry word of an in-domain successor: low 16 bits the signed offset
+// s' - (s + Nc) = dj*Nx + di, high 16 bits the count.  Padding words are 0
+// (offset 0, count 0: a harmless zero term).  The sink's count lives in
+// sinkc[ir], outside the entry pool.
+__device__ __forceinline__ uint32_t entry_word(int off, uint32_t n) {
+  return ((uint32_t)off & 0xFFFFu) | (n << 16);
+}
+
 // Executed by one full warp for one slice.  Lane l owns internal row
 // ir = sl*32 + l.  Scans its histogram column hist[b*32 + l] over the bins of
 // [lo_x, hi_x] x [lo_y, hi_y] (sub-grid offsets) in ascending bin order,
 // zeroes what it reads, classifies each landing cell (outside the domain or an
-// obstacle at t+1 -> sink), stages (bin, count) words in stage[k*32 + l],
+// obstacle at t+1 -> sink), stages entry words in stage[k*32 + l],
 // accumulates R = sum_b (count_b/N) r_b + (count_sink/N) r_outbound in that
 // order, then allocates the slice's columns from the pool and writes them.
 template <typename RT>
@@ -84,7 +92,8 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
   const int q = lane / a.A_pad, act = lane % a.A_pad;
   const int64_t s = sl * a.spw + q;
   const int64_t ir = sl * 32 + lane;
-  int e = 0;
+  int e = 0;              // in-domain entries
+  uint32_t sink = 0;      // realizations ending in the sink
   RT Racc[3] = {RT(0), RT(0), RT(0)};
   bool cap_hit = false;
 
@@ -93,8 +102,7 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
   hi_x = min(hi_x, a.h);
   hi_y = min(hi_y, a.h);
   if (kind == KIND_SINK) {
-    stage[lane] = kSinkBin | (static_cast<uint32_t>(a.N) << 16);
-    e = 1;
+    sink = (uint32_t)a.N;
     for (int o = 0; o < a.rw.n_obj; ++o) {
       if constexpr (sizeof(RT) == 8)
         Racc[o] = __dmul_rn(__ddiv_rn((double)a.N, (double)a.N), a.rw.r_out);
@@ -108,7 +116,6 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
     RT F, g_s = RT(0);
     if constexpr (sizeof(RT) == 8) F = a.act.F64[act]; else F = a.act.F[act];
     if (a.gbar) g_s = load_field<RT>(a.gbar, s);
-    uint32_t sink = 0;
     const RT invN = RT(1) / RT(a.N);
     for (int dj = lo_y; dj <= hi_y; ++dj) {
       const int jp = j + dj;
@@ -131,7 +138,7 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
           cap_hit = true;
           continue;
         }
-        stage[e * 32 + lane] = (uint32_t)b | (n << 16);
+        stage[e * 32 + lane] = entry_word(dj * a.nx + di, n);
         ++e;
         const bool is_t = (ccls & CLS_TARGET) != 0;
         RT g_sp = RT(0);
@@ -148,25 +155,25 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
       }
     }
     if (row_ok && sink > 0) {
-      if (e >= a.row_cap) {
-        cap_hit = true;
-      } else {
-        stage[e * 32 + lane] = kSinkBin | (sink << 16);
-        ++e;
-        for (int o = 0; o < a.rw.n_obj; ++o) {
-          if constexpr (sizeof(RT) == 8) {
-            const double p = __ddiv_rn((double)sink, (double)a.N);
-            Racc[o] = __dadd_rn(Racc[o], __dmul_rn(p, a.rw.r_out));
-          } else {
-            Racc[o] = fmaf((float)sink * invN, (float)a.rw.r_out, Racc[o]);
-          }
+      for (int o = 0; o < a.rw.n_obj; ++o) {
+        if constexpr (sizeof(RT) == 8) {
+          const double p = __ddiv_rn((double)sink, (double)a.N);
+          Racc[o] = __dadd_rn(Racc[o], __dmul_rn(p, a.rw.r_out));
+        } else {
+          Racc[o] = fmaf((float)sink * invN, (float)a.rw.r_out, Racc[o]);
         }
       }
     }
-    if (!row_ok) e = 0;
+    if (!row_ok) {
+      e = 0;
+      sink = 0;
+    }
   }
-  if (cap_hit) atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
-  if (!row_ok && kind == KIND_SAMPLE) e = 0;
+  if (e + (sink > 0 ? 1 : 0) > a.row_cap) cap_hit = true;
+  if (cap_hit) {
+    atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
+    e = 0;
+  }
 
   // slice width = widest row; allocate columns from the pool (bump allocator)
   int W = e;
@@ -184,15 +191,23 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
     uint32_t *dst = a.pool + base * 32 + lane;
     for (int k = 0; k < W; ++k) dst[(size_t)k * 32] = (k < e) ? stage[k * 32 + lane] : 0u;
   }
-  if (lane == 0) a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
-  int tot = e;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
-  if (lane == 0 && tot > 0) {
-    atomicAdd(&a.cnt[CNT_NNZ], (unsigned long long)tot);
-    atomicMax(&a.cnt[CNT_MAXROW], (unsigned long long)W);
+  if (lane == 0) {
+    a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
+    a.slice_w[sl] = (fits && W > 0) ? (uint8_t)W : (uint8_t)0;
   }
   a.nnz[ir] = (uint8_t)e;
+  a.sinkc[ir] = (uint16_t)sink;
+  int tot = e + (sink > 0 ? 1 : 0), dom = e;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    dom += __shfl_xor_sync(0xffffffffu, dom, off);
+  }
+  if (lane == 0 && tot > 0) {
+    atomicAdd(&a.cnt[CNT_NNZ], (unsigned long long)tot);
+    atomicAdd(&a.cnt[CNT_DOMAIN], (unsigned long long)dom);
+    atomicMax(&a.cnt[CNT_MAXROW], (unsigned long long)W);
+  }
   for (int o = 0; o < a.rw.n_obj; ++o) static_cast<RT *>(a.R)[(int64_t)o * a.rows_pad + ir] = Racc[o];
 }
 

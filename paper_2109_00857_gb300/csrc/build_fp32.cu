@@ -90,7 +90,15 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(BuildArgs a) {
   __syncthreads();
 
   for (;;) {
-    if (tid == 0) s_slice = a.slice_begin + (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+    if (tid == 0) {
+      if (a.defer_in) {
+        const unsigned long long i = atomicAdd(&a.cnt[CNT_DEFER_WORK], 1ULL);
+        s_slice = (i < *(volatile unsigned long long *)&a.cnt[CNT_DEFER_N]) ? (long long)a.defer_in[i]
+                                                                              : (long long)a.slice_end;
+      } else {
+        s_slice = a.slice_begin + (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+      }
+    }
     __syncthreads();
     const int64_t sl = s_slice;
     if (sl >= a.slice_end) break;
@@ -225,7 +233,7 @@ static cudaError_t launch_kt(const BuildArgs &a, int threads, int sms, cudaStrea
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t blocks = (int64_t)sms * per_sm;
   const int64_t work = a.slice_end - a.slice_begin;
-  if (blocks > work) blocks = work > 0 ? work : 1;
+  if (!a.defer_in && blocks > work) blocks = work > 0 ? work : 1;
   build_fp32_kernel<KT><<<(unsigned)blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }

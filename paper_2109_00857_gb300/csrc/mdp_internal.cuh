@@ -4,10 +4,12 @@
 //   internal row   ir = s * A_pad + a          (A_pad = A rounded up to a power of two <= 32)
 //   slice          sl = ir / 32 = s / spw      (spw = 32 / A_pad states per slice)
 //   lane           l  = ir % 32 = (s % spw) * A_pad + a
-//   entries        pool[(slice_off[sl] + k) * 32 + l], k < nnz[ir], one 32-bit word each:
-//                  bits 0..15 sub-grid bin b = (dj+h)*L + (di+h)  (0xFFFF = sink),
+//   entries        pool[(slice_off[sl] + k) * 32 + l], k < nnz[ir]: the in-domain
+//                  successors in ascending order, one 32-bit word each (columns
+//                  nnz[ir] .. slice_w[sl]-1 of a row hold 0 = padding):
+//                  bits 0..15 signed offset o = s' - (s + Nc) = dj*Nx + di,
 //                  bits 16..31 count (realizations landing there, <= N <= 65535)
-//   successor      s' = s + Nc + delta[b]      (delta[b] = dj*Nx + di), sink s' = |S|
+//   sink           sinkc[ir] realizations end in the sink s' = |S| (V = 0)
 //   R              R[o * rows_pad + ir]        (float or double), rows_pad = n_slices * 32
 // Warps read a slice column (32 lanes x 4 B = 128 B) per k: fully coalesced.
 #pragma once
@@ -39,6 +41,9 @@ enum {
   CNT_SAMPLES = 6,       // landing evaluations performed
   CNT_NNZ = 7,           // stored entries (sink included)
   CNT_MAXROW = 8,        // widest row
+  CNT_DEFER_N = 9,       // slices the warp kernel handed to the CTA kernel
+  CNT_DEFER_WORK = 10,   // work-queue head of the CTA kernel over the deferred list
+  CNT_DOMAIN = 11,       // stored in-domain successors (sink entries excluded)
   CNT_N = 16
 };
 
@@ -69,11 +74,16 @@ struct BuildArgs {
   uint32_t *pool;
   uint64_t pool_cap_cols;
   uint32_t *slice_off;
+  uint8_t *slice_w;
   uint8_t *nnz;
+  uint16_t *sinkc;
   void *R;
   unsigned long long *cnt;
-  int32_t chunk;             // realizations per staged pass (FP32)
+  int32_t chunk;             // realizations per staged pass (FP32 CTA kernel)
   int64_t slice_begin, slice_end;  // work range [begin, end)
+  int32_t cap_bins;          // per-lane histogram capacity of the warp kernel
+  uint32_t *defer;           // slices deferred by the warp kernel ([n_slices])
+  const uint32_t *defer_in;  // non-NULL: the CTA kernel works on this list (count CNT_DEFER_N)
 };
 
 struct mdp_model_impl;
@@ -90,18 +100,24 @@ struct mdp_model_t {
   uint32_t *pool;
   uint64_t pool_cols;         // columns in use (after compaction: capacity == in use)
   uint32_t *slice_off;
-  uint8_t *nnz;
+  uint8_t *slice_w;           // [n_slices] columns per slice
+  uint8_t *nnz;               // [rows_pad] in-domain entries per row
+  uint16_t *sinkc;            // [rows_pad] realizations ending in the sink
   void *R;                    // [n_obj][rows_pad]
   uint8_t *cls;               // [nt][ny][nx]
-  int32_t *delta;             // [nbins]
+  int32_t *delta;             // [nbins] (unused by the solver)
   void *Vtmp;                 // [nS+1] Jacobi ping-pong partner
   unsigned long long *cnt;    // [CNT_N]
   double *solve_stats_d;      // [4] device scalars for the solver
   int64_t device_bytes;
   int64_t nnz_total;
+  int64_t nnz_domain;
   int32_t max_row_nnz;
   int64_t samples;
   double build_ms;
+  double kernel_ms;
+  int32_t launches;
+  int64_t deferred;           // slices the full-window kernel built
   int device;
 };
 
@@ -129,7 +145,10 @@ cudaError_t launch_sample_coeffs(int nt, int N, int K, const double *sigma_d, ui
                                  uint64_t mdp_id, double *Y64, float *Y32,
                                  unsigned long long *capped, cudaStream_t st);
 // build
+// warp-per-slice kernel (fast path) followed by the CTA kernel over the
+// slices it deferred (histogram wider than cap_bins)
 cudaError_t launch_build_fp32(const BuildArgs &a, int threads, int sms, cudaStream_t st);
+cudaError_t launch_build_warp(const BuildArgs &a, int warps_per_cta, int sms, cudaStream_t st);
 cudaError_t launch_build_fp64(const BuildArgs &a, cudaStream_t st);
 // cell classes + sub-grid delta table
 cudaError_t launch_prepare(const uint8_t *obstacle, const uint8_t *target, uint8_t *cls,
@@ -142,12 +161,15 @@ cudaError_t launch_absmax(const void *x, int precision, int64_t n, int G, int64_
 struct SolveArgs {
   const uint32_t *pool;
   const uint32_t *slice_off;
+  const uint8_t *slice_w;
+  int32_t wcap;               // widest slice (columns)
+  int *err;                   // device error word (bounded waits that expired)
   const uint8_t *nnz;
   const void *R;              // objective slot base
   const uint8_t *cls;
   const int32_t *delta;
   int64_t nS, Nc, n_slices;
-  int32_t A, A_pad, spw, N;
+  int32_t A, A_pad, spw, N, nbins;
   double tol;
 };
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,

@@ -47,7 +47,7 @@ class MdpEnv(C.Structure):
 
 class MdpBuildOpts(C.Structure):
     _fields_ = [("row_cap", C.c_int32), ("no_compact", C.c_int32), ("threads", C.c_int32),
-                ("chunk", C.c_int32)]
+                ("chunk", C.c_int32), ("hist_cap", C.c_int32)]
 
 
 class MdpModelInfo(C.Structure):
@@ -55,7 +55,8 @@ class MdpModelInfo(C.Structure):
                 ("n_obj", C.c_int32), ("objs", C.c_int32 * 3), ("precision", C.c_int32),
                 ("rows", C.c_int64), ("nnz", C.c_int64), ("max_row_nnz", C.c_int32),
                 ("pool_columns", C.c_int64), ("device_bytes", C.c_int64), ("samples", C.c_int64),
-                ("build_ms", C.c_double)]
+                ("build_ms", C.c_double), ("kernel_ms", C.c_double), ("launches", C.c_int32),
+                ("wide_slices", C.c_int64), ("nnz_domain", C.c_int64)]
 
 
 class MdpSolveStats(C.Structure):

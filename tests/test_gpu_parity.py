@@ -179,6 +179,10 @@ FP32_CASES = {
     "A12_ragged": lambda: inputs.make_env(nx=9, ny=7, nt=4, K=3, N=250, L=9, sigma=(0.3, 0.2, 0.1),
                                           seed=5, amplitude=0.8, n_headings=12, n_speeds=1,
                                           obstacle="squares", square=3),
+    "wide_rows_pool_retry": lambda: custom_env(
+        nx=9, ny=9, nt=3, K=2, N=3000, L=15, seed=12, sigma=[1.1, 1.0],
+        modes=np.stack([np.stack([np.ones((3, 9, 9)), np.zeros((3, 9, 9))], -1),
+                        np.stack([np.zeros((3, 9, 9)), np.ones((3, 9, 9))], -1)], 1)),
     "K7_runtime_modes": lambda: inputs.make_env(nx=12, ny=12, nt=4, K=7, N=300, L=15,
                                                 sigma=tuple(0.2 for _ in range(7)), seed=8,
                                                 amplitude=1.0, n_headings=16, n_speeds=2),
@@ -225,6 +229,28 @@ def test_fp32_chunked_realizations_match(mdp):
     for x in outs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(outs[0][:3], x[:3]))
         np.testing.assert_allclose(outs[0][3], x[3], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("case", ["tiny", "energy_small", "three_objectives", "A12_ragged",
+                                  "wide_rows_pool_retry"])
+def test_warp_kernel_and_full_window_kernel_agree_bitwise(mdp, case):
+    """The warp-per-slice kernel and the full-window CTA kernel (used for slices
+    whose histogram does not fit) evaluate the same FP32 operations: forcing
+    every slice through either one gives the same model bit for bit."""
+    env = FP32_CASES[case]()
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    outs = []
+    for cap in (0, 1, 24):
+        o = mdp.MdpBuildOpts()
+        o.hist_cap = cap
+        m = mdp.mdp_build(d, objs=env.objectives, opts=o)
+        info = m.info()
+        if cap == 1:
+            assert info.wide_slices > 0
+        outs.append([export_np(mdp, m, k) for k in range(len(env.objectives))])
+    for x in outs[1:]:
+        for a_, b_ in zip(outs[0], x):
+            assert all(np.array_equal(p, q) for p, q in zip(a_, b_))
 
 
 def test_fp32_build_is_deterministic_across_block_shapes(mdp):
