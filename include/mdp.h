@@ -188,6 +188,25 @@ typedef struct {
 mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol, int32_t max_sweeps,
                      void *V, int16_t *policy, void *stream, mdp_solve_stats *stats);
 
+/* The same Jacobi value iteration as mdp_solve (method MDP_SOLVE_JACOBI),
+ * for callers that may not allocate device memory once they are running:
+ * a real-time replanning loop that must not block or fragment its memory
+ * budget, or a program whose device memory belongs to another allocator.
+ * The paper has no counterpart of this call.  Its scratch (the second value
+ * buffer, the residual slots and status words) is a fixed array inside the
+ * library, 8 MiB + 32 KiB per GPU, held by every GPU that loads the library
+ * until the process exits; it performs no cudaMalloc or cudaFree.
+ * Limits: (|S| + 1) values must fit 8 MiB (at most 2,097,151 states in FP32,
+ * 1,048,575 in FP64_CHECK) and max_sweeps (0 = nt + 1) must be <= 4092;
+ * larger requests return MDP_ERR_ARG with a message (use mdp_solve).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call reuses the same array
+ * and clears what must start at zero, so calls whose work overlaps on the
+ * GPU (on different streams, or from different threads) race and must not
+ * be issued.  Arguments, outputs and errors as in mdp_solve; solve_ms is 0. */
+mdp_status mdp_solve_noalloc(mdp_model m, int32_t obj, double tol, int32_t max_sweeps, void *V,
+                             int16_t *policy, void *stream, mdp_solve_stats *stats);
+
 void mdp_model_free(mdp_model m);
 
 /* DO coefficients alone (step a1): Y[t][w][k] = sigma_h[k] * z with z from the

@@ -27,6 +27,7 @@ UNITS = {
     "build_warp.cu": [],
     "bellman.cu": [],
     "serve.cu": [],
+    "noalloc.cu": [],
     "check_fp64.cu": ["-fmad=false"],
 }
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mdp_export_csr": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
     "mdp_solve": (C.c_int, [P, C.c_int32, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_model_free": (None, [P]),
+    "mdp_solve_noalloc": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
                                     C.c_int32, P, P]),
     "mdp_batch_create": (C.c_int, [P, C.c_int32, C.c_double, P]),
@@ -264,6 +265,25 @@ def mdp_solve(model: Model, obj: int = 0, method: int = MDP_SOLVE_JACOBI, tol: f
     st = MdpSolveStats()
     _check(load().mdp_solve(model.handle, obj, method, float(tol), int(max_sweeps), _ptr(V),
                             _ptr(policy), _stream(stream), C.byref(st)), "mdp_solve")
+    return V, policy, st
+
+
+def mdp_solve_noalloc(model: Model, obj: int = 0, tol: float = 0.0, max_sweeps: int = 0, V=None,
+                      policy=None, stream=None):
+    """Jacobi solve whose scratch is a fixed array inside the library: no device
+    allocation happens in the call (V and policy must be passed in by a caller
+    that cannot allocate; they are allocated here only for convenience when
+    omitted).  Returns (V, policy, MdpSolveStats)."""
+    import torch
+    info = mdp_model_info(model)
+    if V is None:
+        V = torch.empty(info.n_states + 1, dtype=torch.float64 if model.precision else torch.float32,
+                        device="cuda")
+    if policy is None:
+        policy = torch.empty(info.n_states, dtype=torch.int16, device="cuda")
+    st = MdpSolveStats()
+    _check(load().mdp_solve_noalloc(model.handle, obj, float(tol), int(max_sweeps), _ptr(V),
+                                    _ptr(policy), _stream(stream), C.byref(st)), "mdp_solve_noalloc")
     return V, policy, st
 
 
