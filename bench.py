@@ -178,6 +178,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(t_ms, samples, backups, world, device):
+    """Whole-job numbers over ranks: the step time is the slowest rank's, the
+    work is the sum of every rank's (independent instances, weak scaling)."""
+    if world <= 1:
+        return float(t_ms), float(samples), float(backups)
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = torch.tensor([float(samples), float(backups)], dtype=torch.float64, device=device)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0]), float(tsum[1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -260,13 +274,7 @@ def main():
         dist.barrier()
     clocks = clk.stop()
     t_ms = e0.elapsed_time(e1)
-    tt = torch.tensor([t_ms, float(samples), float(backups)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = tt[0:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = tt[1:3].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        t_ms, samples, backups = float(tmax[0]), float(tsum[0]), float(tsum[1])
+    t_ms, samples, backups = aggregate(t_ms, samples, backups, world, "cuda")
     value = samples / (t_ms / 1e3)
     info = rec["info"]
     hbm, sm_mhz, peak_kind = peaks()
