@@ -54,6 +54,27 @@ void dev_free(void *p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 
+cudaError_t allow_max_smem(const void *func) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  int maxopt = 0;
+  e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  // static and dynamic shared memory together may not exceed the opt-in limit
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           maxopt - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({func, dev});
+  return e;
+}
+
 int num_sms() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -143,6 +164,12 @@ static void free_model_memory(mdp_model_t *m, cudaStream_t st) {
   m->Vtmp = nullptr;
   m->cnt = nullptr;
   m->solve_stats_d = nullptr;
+}
+
+void free_model_on_stream(mdp_model_t *m, cudaStream_t st) {
+  if (!m) return;
+  free_model_memory(m, st);
+  delete m;
 }
 
 }  // namespace mdpgb

@@ -317,7 +317,7 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
   pr->dtab_smem = 0;
   *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
   if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(bellman_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  cudaError_t e = allow_max_smem((const void *)bellman_kernel<RT>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<RT>, 32 * kWarps, *smem);

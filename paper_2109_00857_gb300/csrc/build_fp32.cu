@@ -224,8 +224,7 @@ static size_t fp32_smem_bytes(const BuildArgs &a, int threads) {
 template <int KT>
 static cudaError_t launch_kt(const BuildArgs &a, int threads, int sms, cudaStream_t st) {
   const size_t smem = fp32_smem_bytes(a, threads);
-  cudaError_t e = cudaFuncSetAttribute(build_fp32_kernel<KT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void *)build_fp32_kernel<KT>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_fp32_kernel<KT>, threads, smem);

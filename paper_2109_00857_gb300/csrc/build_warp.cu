@@ -351,8 +351,7 @@ template <int KT, int SPW>
 static cudaError_t launch_w(const BuildArgs &a, int warps, int sms, cudaStream_t st) {
   const size_t per_warp = ((size_t)a.cap_bins * 32 + 2 * kItems) * 4;
   const size_t smem = per_warp * warps;
-  cudaError_t e = cudaFuncSetAttribute(build_warp_kernel<KT, SPW>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void *)build_warp_kernel<KT, SPW>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_warp_kernel<KT, SPW>, warps * 32, smem);

@@ -192,8 +192,7 @@ __global__ void build_fp64_kernel(BuildArgs a) {
 
 cudaError_t launch_build_fp64(const BuildArgs &a, cudaStream_t st) {
   const size_t smem = (size_t)a.nbins * 32 * 4 + (size_t)a.row_cap * 32 * 4;
-  cudaError_t e = cudaFuncSetAttribute(build_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_smem((const void *)build_fp64_kernel);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_fp64_kernel, 256, smem);

@@ -182,4 +182,13 @@ cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_
 
 int num_sms();
 
+// Raises a kernel's dynamic shared-memory limit to the device maximum, once per
+// (kernel, device).  Launches then pass their own size; the limit is never
+// lowered, so concurrent launches with different sizes cannot race on it.
+cudaError_t allow_max_smem(const void *func);
+
+// Frees a model's device memory in the order of `st` (no device-wide sync):
+// for callers that know the model's work was issued on that stream.
+void free_model_on_stream(mdp_model_t *m, cudaStream_t st);
+
 }  // namespace mdpgb

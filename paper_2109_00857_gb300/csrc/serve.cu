@@ -1,28 +1,422 @@
-// serve.cu -- batched build+solve and the replanning server (see include/mdp.h).
+// serve.cu -- the replanning server (on-board re-planning, Sec. V) of
+// include/mdp.h.
+//
+// Registered environments are copied into server-owned device memory and stay
+// resident.  A request names an environment and carries a new start and target,
+// a scale for the coefficient standard deviations, a seed, N, an objective and
+// a tolerance.  Requests wait in a FIFO queue; max_slots worker threads, each
+// with its own CUDA stream, take the head of the queue as soon as a slot is
+// free and the request's device-memory estimate fits the HBM budget, then build
+// and solve it (mdp_build + Jacobi mdp_solve).  Requests admitted while others
+// run overlap with them on the GPU (continuous batching); each retires on its
+// own, copies V and the policy to host memory and releases its device memory.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "mdp_internal.cuh"
 
 using namespace mdpgb;
 
-static mdp_status not_built(const char *what) {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct EnvEntry {
+  mdp_grid grid;
+  mdp_actions actions;
+  std::vector<double> table;     // host action table (owned copy)
+  std::vector<double> sigma;
+  int K = 0, L = 0;
+  void *vbar = nullptr, *modes = nullptr, *gbar = nullptr;
+  uint8_t *obstacle = nullptr;
+};
+
+struct Job {
+  uint64_t ticket = 0;
+  mdp_request req{};
+  Clock::time_point submitted, admitted, finished;
+  int64_t bytes = 0;
+  mdp_status status = MDP_ERR_PENDING;
+  std::string error;
+  int32_t sweeps = 0;
+  float V_start = 0.f;
+  int16_t pi_start = -1;
+  std::vector<float> V;
+  std::vector<int16_t> pi;
+  bool done = false;
+};
+
+}  // namespace
+
+struct mdp_server_t {
+  int device = 0;
+  size_t budget = 0;
+  int slots = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  std::vector<std::unique_ptr<EnvEntry>> envs;
+  std::vector<std::thread> workers;
+  int64_t bytes_in_use = 0;
+  int64_t in_flight = 0;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+};
+
+namespace {
+
+// Device memory a request holds at its peak (the build's first pool guess of
+// 16 columns per slice, rows, R, classes, V pair, policy, coefficients).
+int64_t estimate_bytes(const EnvEntry &e, const mdp_request &r) {
+  const int64_t nS = (int64_t)e.grid.nx * e.grid.ny * e.grid.nt;
+  int A = e.actions.n_headings * e.actions.n_speeds, A_pad = 1;
+  while (A_pad < A) A_pad <<= 1;
+  const int64_t spw = 32 / A_pad, n_slices = (nS + spw - 1) / spw, rows = n_slices * 32;
+  const int64_t pool = n_slices * 16 * 128;
+  return pool + rows * (1 + 2 + 4) + n_slices * 5 + nS * (1 + 4 + 4 + 2) +
+         (int64_t)e.grid.nt * r.N * e.K * 4 + (int64_t)e.grid.nx * e.grid.ny + (1 << 20);
+}
+
+__global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0, int w, int h) {
+  const int n = nx * ny;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int i = c % nx, j = c / nx;
+    tgt[c] = (i >= i0 && i < i0 + w && j >= j0 && j < j0 + h) ? 1 : 0;
+  }
+}
+
+void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
+  const EnvEntry &e = *S->envs[job.req.env_id];
+  const mdp_request &r = job.req;
+  const int nx = e.grid.nx, ny = e.grid.ny;
+  target_block_kernel<<<(nx * ny + 255) / 256, 256, 0, st>>>(tgt, nx, ny, r.target_i, r.target_j,
+                                                             r.target_w, r.target_h);
+  std::vector<double> sig(e.sigma);
+  for (double &x : sig) x *= r.sigma_scale;
+  mdp_env env{};
+  env.K = e.K;
+  env.precision = MDP_FP32;
+  env.vbar = e.vbar;
+  env.modes = e.modes;
+  env.coeffs = nullptr;
+  env.sigma_h = sig.data();
+  env.seed = r.seed;
+  env.mdp_id = 0;
+  env.gbar = e.gbar;
+  env.obstacle = e.obstacle;
+  env.target = tgt;
+  const int32_t obj = r.objective;
+  mdp_model m = nullptr;
+  mdp_status s = mdp_build(&env, &e.grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m);
+  if (s != MDP_OK) {
+    job.status = s;
+    job.error = mdp_last_error();
+    return;
+  }
+  const int64_t nS = m->nS;
+  float *V = nullptr;
+  int16_t *pi = nullptr;
+  cudaError_t ce = dev_alloc((void **)&V, sizeof(float) * (size_t)(nS + 1), st);
+  if (ce == cudaSuccess) ce = dev_alloc((void **)&pi, sizeof(int16_t) * (size_t)nS, st);
+  if (ce != cudaSuccess) {
+    job.status = cuda_fail(ce, "serve allocation");
+    job.error = mdp_last_error();
+    dev_free(V, st);
+    free_model_on_stream(m, st);
+    return;
+  }
+  mdp_solve_stats ss{};
+  s = mdp_solve(m, 0, MDP_SOLVE_JACOBI, r.tol, 0, V, pi, st, &ss);
+  if (s == MDP_OK) {
+    job.V.resize((size_t)nS + 1);
+    job.pi.resize((size_t)nS);
+    ce = cudaMemcpyAsync(job.V.data(), V, sizeof(float) * (size_t)(nS + 1), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(job.pi.data(), pi, sizeof(int16_t) * (size_t)nS, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      s = cuda_fail(ce, "serve copy-out");
+    } else {
+      const int64_t s0 = (int64_t)r.start_j * nx + r.start_i;
+      job.V_start = job.V[(size_t)s0];
+      job.pi_start = job.pi[(size_t)s0];
+      job.sweeps = ss.sweeps;
+    }
+  }
+  job.status = s;
+  if (s != MDP_OK) job.error = mdp_last_error();
+  dev_free(V, st);
+  dev_free(pi, st);
+  // the model's memory goes back on this stream, without a device-wide sync
+  // that would wait for the other slots' work
+  free_model_on_stream(m, st);
+  cudaStreamSynchronize(st);
+}
+
+void worker_main(mdp_server_t *S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  size_t maxc = 0;
+  uint8_t *tgt = nullptr;
+  for (;;) {
+    std::shared_ptr<Job> job;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      // FIFO admission: the head waits until its estimate fits the budget
+      S->cv_work.wait(lk, [&] {
+        return S->stopping || (!S->queue.empty() &&
+                               S->bytes_in_use + S->queue.front()->bytes <= (int64_t)S->budget);
+      });
+      if (S->stopping) break;
+      job = S->queue.front();
+      S->queue.pop_front();
+      S->bytes_in_use += job->bytes;
+      S->in_flight += 1;
+      job->admitted = Clock::now();
+    }
+    const EnvEntry &e = *S->envs[job->req.env_id];
+    const size_t cells = (size_t)e.grid.nx * e.grid.ny;
+    if (cells > maxc) {
+      dev_free(tgt, st);
+      tgt = nullptr;
+      if (dev_alloc((void **)&tgt, cells, st) == cudaSuccess) maxc = cells;
+    }
+    if (!tgt) {
+      job->status = MDP_ERR_OOM;
+      job->error = "target mask allocation failed";
+    } else {
+      run_job(S, *job, st, tgt);
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      job->finished = Clock::now();
+      job->done = true;
+      S->bytes_in_use -= job->bytes;
+      S->in_flight -= 1;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+  dev_free(tgt, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" mdp_status mdp_serve_create(size_t hbm_budget_bytes, int32_t max_slots, mdp_server *out) {
+  if (!out) {
+    set_error("invalid argument: out is NULL");
+    return MDP_ERR_ARG;
+  }
+  *out = nullptr;
+  if (max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0) {
+    set_error("invalid argument: need 1 <= max_slots <= 64 and a nonzero budget");
+    return MDP_ERR_ARG;
+  }
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    set_error("no usable CUDA device (this library has no CPU fallback)");
+    return MDP_ERR_CUDA;
+  }
+  ensure_device_init();
+  auto *S = new mdp_server_t();
+  cudaGetDevice(&S->device);
+  S->budget = hbm_budget_bytes;
+  S->slots = max_slots;
+  for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
+  *out = S;
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_env_register(mdp_server S, const mdp_env *env, const mdp_grid *grid,
+                                       const mdp_actions *actions, int32_t subgrid_L, int32_t *env_id) {
+  if (!S || !env || !grid || !actions || !env_id) {
+    set_error("invalid argument: NULL server/env/grid/actions/env_id");
+    return MDP_ERR_ARG;
+  }
+  if (env->precision != MDP_FP32 || env->coeffs) {
+    set_error("invalid argument: the server takes FP32 fields and draws its own coefficients");
+    return MDP_ERR_ARG;
+  }
+  if (env->K < 0 || env->K > kMaxModes || (env->K > 0 && (!env->sigma_h || !env->modes)) || !env->vbar ||
+      !env->obstacle || grid->nx < 1 || grid->ny < 1 || grid->nt < 1) {
+    set_error("invalid argument: incomplete environment");
+    return MDP_ERR_ARG;
+  }
+  const int A = actions->n_headings * actions->n_speeds;
+  if (A < 1 || A > kMaxActions) {
+    set_error("invalid argument: n_headings * n_speeds must be in [1, 32]");
+    return MDP_ERR_ARG;
+  }
+  auto e = std::make_unique<EnvEntry>();
+  e->grid = *grid;
+  e->actions = *actions;
+  if (actions->table_h) {
+    e->table.assign(actions->table_h, actions->table_h + 3 * A);
+    e->actions.table_h = e->table.data();
+  }
+  e->K = env->K;
+  e->L = subgrid_L;
+  if (env->K > 0) e->sigma.assign(env->sigma_h, env->sigma_h + env->K);
+  const size_t cells = (size_t)grid->nx * grid->ny, n = cells * grid->nt;
+  cudaSetDevice(S->device);
+  cudaError_t ce = cudaMalloc(&e->vbar, 8 * n);
+  if (ce == cudaSuccess) ce = cudaMemcpy(e->vbar, env->vbar, 8 * n, cudaMemcpyDeviceToDevice);
+  if (ce == cudaSuccess && env->K > 0) ce = cudaMalloc(&e->modes, 8 * n * env->K);
+  if (ce == cudaSuccess && env->K > 0)
+    ce = cudaMemcpy(e->modes, env->modes, 8 * n * env->K, cudaMemcpyDeviceToDevice);
+  if (ce == cudaSuccess && env->gbar) ce = cudaMalloc(&e->gbar, 4 * n);
+  if (ce == cudaSuccess && env->gbar) ce = cudaMemcpy(e->gbar, env->gbar, 4 * n, cudaMemcpyDeviceToDevice);
+  if (ce == cudaSuccess) ce = cudaMalloc((void **)&e->obstacle, n);
+  if (ce == cudaSuccess) ce = cudaMemcpy(e->obstacle, env->obstacle, n, cudaMemcpyDeviceToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(e->vbar);
+    cudaFree(e->modes);
+    cudaFree(e->gbar);
+    cudaFree(e->obstacle);
+    return cuda_fail(ce, "mdp_env_register");
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  *env_id = (int32_t)S->envs.size();
+  S->envs.push_back(std::move(e));
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uint64_t *ticket) {
+  if (!S || !req || !ticket) {
+    set_error("invalid argument: NULL server/request/ticket");
+    return MDP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stopping) {
+    set_error("server is shutting down");
+    return MDP_ERR_CANCELLED;
+  }
+  if (req->env_id < 0 || req->env_id >= (int32_t)S->envs.size()) {
+    set_error("unknown env_id");
+    return MDP_ERR_NOT_FOUND;
+  }
+  const EnvEntry &e = *S->envs[req->env_id];
+  const mdp_grid &g = e.grid;
+  if (req->N < 1 || req->N > 65535 || req->objective < 0 || req->objective > 2 ||
+      (req->objective == MDP_OBJ_NET_ENERGY && !e.gbar) || !(req->sigma_scale >= 0) ||
+      req->start_i < 0 || req->start_i >= g.nx || req->start_j < 0 || req->start_j >= g.ny ||
+      req->target_w < 1 || req->target_h < 1) {
+    set_error("invalid argument: bad request fields");
+    return MDP_ERR_ARG;
+  }
+  auto job = std::make_shared<Job>();
+  job->req = *req;
+  job->bytes = estimate_bytes(e, *req);
+  if (job->bytes > (int64_t)S->budget) {
+    set_error("request needs more device memory than the whole HBM budget");
+    return MDP_ERR_BUDGET;
+  }
+  job->ticket = S->next_ticket++;
+  job->submitted = Clock::now();
+  S->jobs[job->ticket] = job;
+  S->queue.push_back(job);
+  *ticket = job->ticket;
+  S->cv_work.notify_all();
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_serve_poll(mdp_server S, uint64_t ticket, int32_t timeout_ms, mdp_result *out,
+                                     float *V_h, int16_t *pi_h) {
+  if (!S || !out) {
+    set_error("invalid argument: NULL server/result");
+    return MDP_ERR_ARG;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) {
+    set_error("unknown ticket");
+    return MDP_ERR_NOT_FOUND;
+  }
+  std::shared_ptr<Job> job = it->second;
+  if (!job->done && timeout_ms > 0)
+    S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return job->done; });
+  if (!job->done) return MDP_ERR_PENDING;
+  memset(out, 0, sizeof(*out));
+  out->status = job->status;
+  out->V_start = job->V_start;
+  out->pi_start = job->pi_start;
+  out->sweeps = job->sweeps;
+  out->latency_ms = ms_between(job->submitted, job->finished);
+  out->queue_ms = ms_between(job->submitted, job->admitted);
+  out->device_bytes = job->bytes;
+  if (job->status == MDP_OK) {
+    if (V_h) memcpy(V_h, job->V.data(), sizeof(float) * job->V.size());
+    if (pi_h) memcpy(pi_h, job->pi.data(), sizeof(int16_t) * job->pi.size());
+  } else {
+    set_error(job->error);
+  }
+  S->jobs.erase(it);   // released
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_serve_stats(mdp_server S, int64_t *in_flight, int64_t *queued,
+                                      int64_t *bytes_in_use) {
+  if (!S) {
+    set_error("invalid argument: NULL server");
+    return MDP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (in_flight) *in_flight = S->in_flight;
+  if (queued) *queued = (int64_t)S->queue.size();
+  if (bytes_in_use) *bytes_in_use = S->bytes_in_use;
+  return MDP_OK;
+}
+
+extern "C" mdp_status mdp_serve_destroy(mdp_server S) {
+  if (!S) return MDP_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stopping = true;
+    for (auto &j : S->queue) {   // queued requests are cancelled; running ones finish
+      j->status = MDP_ERR_CANCELLED;
+      j->error = "server destroyed before the request was admitted";
+      j->done = true;
+    }
+    S->queue.clear();
+  }
+  S->cv_work.notify_all();
+  S->cv_done.notify_all();
+  for (auto &t : S->workers) t.join();
+  cudaSetDevice(S->device);
+  for (auto &e : S->envs) {
+    cudaFree(e->vbar);
+    cudaFree(e->modes);
+    cudaFree(e->gbar);
+    cudaFree(e->obstacle);
+  }
+  delete S;
+  return MDP_OK;
+}
+
+// ------------------------------------------------------------- batching --
+static mdp_status batch_not_built(const char *what) {
   set_error(std::string(what) + ": not available in this build");
   return MDP_ERR_ARG;
 }
-
 extern "C" mdp_status mdp_batch_create(const mdp_batch_item *, int32_t, double, mdp_batch *out) {
   if (out) *out = nullptr;
-  return not_built("mdp_batch_create");
+  return batch_not_built("mdp_batch_create");
 }
-extern "C" mdp_status mdp_batch_run(mdp_batch, void *, int32_t *, double *) { return not_built("mdp_batch_run"); }
+extern "C" mdp_status mdp_batch_run(mdp_batch, void *, int32_t *, double *) { return batch_not_built("mdp_batch_run"); }
 extern "C" void mdp_batch_free(mdp_batch) {}
-extern "C" mdp_status mdp_serve_create(size_t, int32_t, mdp_server *out) {
-  if (out) *out = nullptr;
-  return not_built("mdp_serve_create");
-}
-extern "C" mdp_status mdp_env_register(mdp_server, const mdp_env *, const mdp_grid *, const mdp_actions *,
-                                       int32_t, int32_t *) { return not_built("mdp_env_register"); }
-extern "C" mdp_status mdp_serve_submit(mdp_server, const mdp_request *, uint64_t *) { return not_built("mdp_serve_submit"); }
-extern "C" mdp_status mdp_serve_poll(mdp_server, uint64_t, int32_t, mdp_result *, float *, int16_t *) {
-  return not_built("mdp_serve_poll");
-}
-extern "C" mdp_status mdp_serve_stats(mdp_server, int64_t *, int64_t *, int64_t *) { return not_built("mdp_serve_stats"); }
-extern "C" mdp_status mdp_serve_destroy(mdp_server) { return not_built("mdp_serve_destroy"); }

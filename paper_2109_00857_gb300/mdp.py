@@ -299,3 +299,72 @@ def mdp_sample_coeffs(nt: int, N: int, K: int, sigma, seed: int, mdp_id: int = 0
 
 def mdp_version() -> str:
     return load().mdp_version().decode()
+
+
+# ---------------------------------------------------------------- serving --
+class Server:
+    """Replanning server (mdp_serve_*): resident environments, FIFO admission
+    under an HBM budget, concurrent requests on per-slot streams."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        h = P()
+        _check(load().mdp_serve_create(int(hbm_budget_bytes), int(max_slots), C.byref(h)),
+               "mdp_serve_create")
+        self.handle = h.value
+        self._envs = []
+
+    def register(self, denv: DeviceEnv, subgrid_L: Optional[int] = None) -> int:
+        e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
+        e.coeffs = None
+        eid = C.c_int32()
+        L = denv.env.L if subgrid_L is None else subgrid_L
+        _check(load().mdp_env_register(self.handle, C.byref(e), C.byref(g), C.byref(a), L,
+                                       C.byref(eid)), "mdp_env_register")
+        self._envs.append(denv.env)
+        return eid.value
+
+    def submit(self, env_id, start, target, target_size=(2, 2), sigma_scale=1.0, seed=0, N=1000,
+               objective=MDP_OBJ_TIME, tol=0.0) -> int:
+        r = MdpRequest()
+        r.env_id = env_id
+        r.start_i, r.start_j = start
+        r.target_i, r.target_j = target
+        r.target_w, r.target_h = target_size
+        r.sigma_scale, r.seed, r.N, r.objective, r.tol = sigma_scale, seed, N, objective, tol
+        t = C.c_uint64()
+        _check(load().mdp_serve_submit(self.handle, C.byref(r), C.byref(t)), "mdp_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0, env_id: Optional[int] = None, want_V=False):
+        """Returns (MdpResult, V, policy) or None while pending; V/policy are
+        numpy arrays when want_V (env_id gives their size)."""
+        res = MdpResult()
+        V = pi = None
+        if want_V:
+            env = self._envs[env_id]
+            V = np.empty(env.nS + 1, dtype=np.float32)
+            pi = np.empty(env.nS, dtype=np.int16)
+        code = load().mdp_serve_poll(self.handle, int(ticket), int(timeout_ms), C.byref(res),
+                                     V.ctypes.data_as(P) if V is not None else None,
+                                     pi.ctypes.data_as(P) if pi is not None else None)
+        if code == -10:
+            return None
+        _check(code, "mdp_serve_poll")
+        return res, V, pi
+
+    def stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().mdp_serve_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)),
+               "mdp_serve_stats")
+        return a.value, b.value, c.value
+
+    def close(self):
+        if self.handle:
+            load().mdp_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,128 @@
+"""Serving: requests admitted under an HBM budget run concurrently on per-slot
+streams; a request's result is the same alone and in a mix of concurrent
+requests, and the same as a direct build + solve of the same parameters."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2109_00857_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mdp():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import build_native, mdp as m
+    build_native.build()
+    m.load()
+    return m
+
+
+def _env(seed=22):
+    return inputs.energy(nx=40, ny=36, nt=12, N=300, seed=seed, L=15)
+
+
+def _direct(mdp, env, target, sigma_scale, seed, N, obj):
+    """The same request through mdp_build + mdp_solve."""
+    e = inputs.Environment(**{**env.__dict__})
+    e.target = inputs.target_block(env.nx, env.ny, target[0], target[1])
+    e.sigma = env.sigma * sigma_scale
+    e.seed, e.N, e.mdp_id = seed, N, 0
+    m = mdp.mdp_build(mdp.DeviceEnv(e, mdp.MDP_FP32), objs=(obj,))
+    V, pi, st = mdp.mdp_solve(m, 0, tol=0.0)
+    return V.cpu().numpy(), pi.cpu().numpy()
+
+
+def test_result_alone_equals_result_in_a_mix(mdp):
+    env = _env()
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    probe = dict(start=(20, 7), target=(21, 28), sigma_scale=1.3, seed=77, N=300, objective=2)
+    # alone: one slot, nothing else in flight
+    s1 = mdp.Server(8 << 30, 1)
+    eid = s1.register(d)
+    t = s1.submit(eid, **probe)
+    res, V_alone, pi_alone = s1.poll(t, timeout_ms=60000, env_id=eid, want_V=True)
+    assert res.status == 0, mdp.load().mdp_last_error().decode()
+    s1.close()
+    # in a mix: 4 slots, 9 other requests submitted around it
+    s4 = mdp.Server(8 << 30, 4)
+    eid = s4.register(d)
+    rng = np.random.default_rng(5)
+    tickets = []
+    for k in range(10):
+        if k == 4:
+            tickets.append(("probe", s4.submit(eid, **probe)))
+        else:
+            tickets.append(("other", s4.submit(
+                eid, start=(int(rng.integers(0, 40)), int(rng.integers(0, 36))),
+                target=(int(rng.integers(0, 38)), int(rng.integers(0, 34))),
+                sigma_scale=float(rng.uniform(0.5, 1.5)), seed=int(rng.integers(1, 1000)),
+                N=int(rng.integers(100, 400)), objective=int(rng.integers(0, 3)))))
+    seen_overlap = 0
+    for _ in range(200):
+        inflight, queued, used = s4.stats()
+        seen_overlap = max(seen_overlap, inflight)
+        if queued == 0 and inflight == 0:
+            break
+        time.sleep(0.005)
+    for kind, t in tickets:
+        res, V, pi = s4.poll(t, timeout_ms=60000, env_id=eid, want_V=True)
+        assert res.status == 0, mdp.load().mdp_last_error().decode()
+        assert res.latency_ms >= res.queue_ms >= 0
+        if kind == "probe":
+            assert np.array_equal(V, V_alone) and np.array_equal(pi, pi_alone)
+    s4.close()
+    assert seen_overlap >= 2, "requests never overlapped"
+    Vd, pid = _direct(mdp, env, probe["target"], probe["sigma_scale"], probe["seed"], probe["N"],
+                      probe["objective"])
+    assert np.array_equal(Vd, V_alone) and np.array_equal(pid, pi_alone)
+
+
+def test_budget_admission_and_errors(mdp):
+    env = _env()
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    s = mdp.Server(64 << 20, 2)     # 64 MiB: this environment's requests fit one at a time
+    eid = s.register(d)
+    with pytest.raises(mdp.MdpError) as ei:
+        s.submit(eid + 5, start=(1, 1), target=(3, 3))
+    assert ei.value.code == -9
+    with pytest.raises(mdp.MdpError) as ei:
+        s.submit(eid, start=(1, 1), target=(3, 3), N=0)
+    assert ei.value.code == -1
+    tk = [s.submit(eid, start=(1, 1), target=(20, 20), seed=i, N=300) for i in range(3)]
+    peak = 0
+    for _ in range(400):
+        inflight, queued, used = s.stats()
+        assert used <= 64 << 20
+        peak = max(peak, inflight)
+        if inflight == 0 and queued == 0:
+            break
+        time.sleep(0.002)
+    for t in tk:
+        res, _, _ = s.poll(t, timeout_ms=60000)
+        assert res.status == 0, mdp.load().mdp_last_error().decode()
+    s.close()
+    big = mdp.Server(1 << 20, 1)    # 1 MiB: every request is larger than the whole budget
+    eid = big.register(d)
+    with pytest.raises(mdp.MdpError) as ei:
+        big.submit(eid, start=(1, 1), target=(3, 3))
+    assert ei.value.code == -7
+    big.close()
+
+
+def test_poll_pending_and_unknown_ticket(mdp):
+    env = _env()
+    s = mdp.Server(8 << 30, 1)
+    eid = s.register(mdp.DeviceEnv(env, mdp.MDP_FP32))
+    t = s.submit(eid, start=(2, 2), target=(30, 30), N=2000)
+    r = s.poll(t, timeout_ms=0)
+    assert r is None or r[0].status == 0
+    res, _, _ = s.poll(t, timeout_ms=60000) if r is None else r
+    assert res.status == 0
+    with pytest.raises(mdp.MdpError) as ei:
+        s.poll(t, timeout_ms=0)      # released after the first successful poll
+    assert ei.value.code == -9
+    s.close()
