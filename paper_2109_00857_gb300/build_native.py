@@ -28,6 +28,7 @@ UNITS = {
     "bellman.cu": [],
     "serve.cu": [],
     "noalloc.cu": [],
+    "batch.cu": [],
     "check_fp64.cu": ["-fmad=false"],
 }
 

@@ -206,9 +206,14 @@ extern "C" mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const 
   return MDP_OK;
 }
 
-extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
-                                int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
-                                const mdp_build_opts *opts, void *stream, mdp_model *out) {
+namespace mdpgb {
+// The whole build.  With a hook, it stops after the set-up (validation,
+// coefficient draw, sub-grid size, allocations, cell classes) and hands the
+// model and its kernel arguments to the caller instead of launching the build
+// (the batched build launches them itself).
+mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
+                      int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,
+                      void *stream, mdp_model *out, BuildHook *hook) {
   if (out) *out = nullptr;
   mdp_status s = check_device();
   if (s != MDP_OK) return s;
@@ -351,7 +356,7 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
     if (c > budget_cols) c = budget_cols;
     return c < 1 ? (uint64_t)1 : c;
   };
-  uint64_t cap_cols = pool_cols_for(kPoolGuess);
+  uint64_t cap_cols = (hook && hook->pool_cols) ? hook->pool_cols : pool_cols_for(kPoolGuess);
   TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
   TRY(dev_alloc((void **)&m->slice_off, sizeof(uint32_t) * (size_t)m->n_slices, st));
   TRY(dev_alloc((void **)&m->slice_w, (size_t)m->n_slices, st));
@@ -386,6 +391,19 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   ba.cap_bins = hist_cap;
   ba.defer = defer;
   ba.defer_in = nullptr;
+  if (hook) {
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaEventDestroy(evk);
+    hook->args = ba;
+    hook->Yown = Yown;
+    hook->sigma_d = sig_d;
+    hook->defer = defer;
+    hook->pool_cols = cap_cols;
+    hook->threads = threads;
+    *out = m;
+    return MDP_OK;
+  }
   static thread_local Pinned pin;
   if (!pin.p) return fail(cuda_fail(cudaErrorMemoryAllocation, "cudaMallocHost"));
   const unsigned long long *c = pin.p;
@@ -465,6 +483,14 @@ extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const 
   *out = m;
 #undef TRY
   return MDP_OK;
+}
+
+}  // namespace mdpgb
+
+extern "C" mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
+                                int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                                const mdp_build_opts *opts, void *stream, mdp_model *out) {
+  return build_impl(env, grid, actions, N, subgrid_L, objs_h, n_obj, opts, stream, out, nullptr);
 }
 
 extern "C" mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *o) {

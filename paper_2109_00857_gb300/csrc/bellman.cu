@@ -150,23 +150,17 @@ static int stage_bytes_for(int wcap, size_t rsz) {
 // and widths of the next 32 slices are read in one coalesced load.
 // res != nullptr: Jacobi sweep k (exits at once if sweep k-1 met the
 // tolerance) with the residual reduced into res[k-1].
+// One CTA, slices [b_lo, b_hi) of one model (all threads call it).
 template <typename RT>
-__global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, const RT *Vin, RT *Vout,
-                                                              int16_t *policy, unsigned long long *res, int k,
-                                                              PipeRange pr) {
+__device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, RT *Vout, int16_t *policy,
+                                             unsigned long long *res, int k, int64_t b_lo, int64_t b_hi,
+                                             const PipeRange &pr, unsigned char *sm, double *wmax,
+                                             int *wst_s) {
   if (res && k > 1 && __longlong_as_double((long long)res[k - 2]) <= a.tol) return;
   if (*(volatile int *)a.err) return;   // an earlier launch of this solve timed out
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ double wmax[kWarps];
-  __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
   uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // [kWarps][kDepth]
   unsigned char *ring = sm + 256;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  const int64_t total = pr.sl_hi - pr.sl_lo;
-  const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
-  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
-  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
   const int64_t n_local = b_hi - b_lo;
   if (n_local <= 0) return;
 
@@ -287,6 +281,81 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, co
       if (m > 0.0) atomicMax(&res[k - 1], (unsigned long long)__double_as_longlong(m));
     }
   }
+}
+
+template <typename RT>
+__global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, const RT *Vin, RT *Vout,
+                                                              int16_t *policy, unsigned long long *res, int k,
+                                                              PipeRange pr) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWarps];
+  __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
+  const int64_t total = pr.sl_hi - pr.sl_lo;
+  const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
+  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
+  bellman_body<RT>(a, Vin, Vout, policy, res, k, b_lo, b_hi, pr, sm, wmax, wst_s);
+}
+
+// Batched Jacobi sweep k over many models: CTA b works on ctas[b] (one
+// model's contiguous slice range); each model stops on its own residual.
+__global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const BatchSolveItem *items,
+                                                                    const BatchCta *ctas, int k,
+                                                                    int stage_bytes) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWarps];
+  __shared__ int wst_s[kWarps * kDepth];
+  const BatchCta c = ctas[blockIdx.x];
+  const BatchSolveItem &it = items[c.item];
+  if (k > it.max_sweeps) return;
+  PipeRange pr;
+  pr.sl_lo = c.sl_lo;
+  pr.sl_hi = c.sl_hi;
+  pr.s_lo = 0;
+  pr.s_hi = it.a.nS;
+  pr.stage_bytes = stage_bytes;
+  pr.dtab_smem = 0;
+  const float *vin = (k & 1) ? it.Va : it.Vb;
+  float *vout = (k & 1) ? it.Vb : it.Va;
+  bellman_body<float>(it.a, vin, vout, it.policy, it.res, k, c.sl_lo, c.sl_hi, pr, sm, wmax, wst_s);
+}
+
+// Per model (one block each): sweeps and residual, final iterate into Va.
+__global__ void finalize_batch_kernel(const BatchSolveItem *items) {
+  const BatchSolveItem &it = items[blockIdx.x];
+  __shared__ int s_sweeps;
+  if (threadIdx.x == 0) {
+    int sw = it.max_sweeps;
+    for (int k = 1; k <= it.max_sweeps; ++k)
+      if (__longlong_as_double((long long)it.res[k - 1]) <= it.a.tol) { sw = k; break; }
+    s_sweeps = sw;
+    it.stats[0] = (double)sw;
+    it.stats[1] = sw > 0 ? __longlong_as_double((long long)it.res[sw - 1]) : 0.0;
+  }
+  __syncthreads();
+  if ((s_sweeps & 1) == 0) return;
+  for (int64_t i = threadIdx.x; i <= it.a.nS; i += blockDim.x) it.Va[i] = it.Vb[i];
+}
+
+cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, const BatchCta *ctas_d, int n_ctas, int k,
+                                 int stage_bytes, cudaStream_t st) {
+  const size_t smem = 256 + (size_t)kWarps * kDepth * stage_bytes;
+  bellman_batch_kernel<<<n_ctas, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st) {
+  finalize_batch_kernel<<<n, 256, 0, st>>>(items_d);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm) {
+  *stage_bytes = stage_bytes_for(wcap, 4);
+  const size_t smem = 256 + (size_t)kWarps * kDepth * (*stage_bytes);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = allow_max_smem((const void *)bellman_batch_kernel);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bellman_batch_kernel, 32 * kWarps, smem);
 }
 
 // stats_d[0] = sweeps, [1] = residual of the last sweep.  Copies the final

@@ -55,14 +55,14 @@ __device__ __forceinline__ void load_y(const float *__restrict__ yw, float (&y)[
 }
 
 // KT > 0: the number of modes is a compile-time constant; KT == 0: runtime K.
+// The whole CTA algorithm for one model: all threads of the CTA call it.
+// s_slice is a __shared__ word of the calling kernel.
 template <int KT>
-__global__ void __launch_bounds__(512) build_fp32_kernel(BuildArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
+__device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long long &s_slice) {
   uint32_t *hist = smem;                                             // [nbins][32]
   uint32_t *stage = hist + (size_t)a.nbins * 32;                     // [row_cap][32]
   float2 *ubuf = reinterpret_cast<float2 *>(stage + (size_t)a.row_cap * 32);  // [chunk][spw]
   float *red = reinterpret_cast<float *>(ubuf + (size_t)a.chunk * a.spw);    // [nwarps][spw][4]
-  __shared__ long long s_slice;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -216,7 +216,40 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(BuildArgs a) {
   }
 }
 
-static size_t fp32_smem_bytes(const BuildArgs &a, int threads) {
+template <int KT>
+__global__ void __launch_bounds__(512) build_fp32_kernel(BuildArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ long long s_slice;
+  cta_run<KT>(a, smem, s_slice);
+}
+
+
+// Many models: every CTA walks the models in order and helps finish each
+// model's deferred list (items carry defer_in = their own list).
+__global__ void __launch_bounds__(512) build_fp32_batch_kernel(const BuildArgs *__restrict__ items, int n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ long long s_slice;
+  for (int m = 0; m < n; ++m) {
+    const BuildArgs &a = items[m];
+    if (*(volatile unsigned long long *)&a.cnt[CNT_DEFER_N] == 0) continue;   // same value in every thread
+    cta_run<0>(a, smem, s_slice);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_build_fp32_batch(const BuildArgs *items_d, int n, size_t smem, int threads,
+                                    cudaStream_t st) {
+  cudaError_t e = allow_max_smem((const void *)build_fp32_batch_kernel);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_fp32_batch_kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  build_fp32_batch_kernel<<<num_sms() * per_sm, threads, smem, st>>>(items_d, n);
+  return cudaGetLastError();
+}
+
+size_t fp32_smem_bytes(const BuildArgs &a, int threads) {
   return (size_t)a.nbins * 32 * 4 + (size_t)a.row_cap * 32 * 4 + (size_t)a.chunk * a.spw * 8 +
          (size_t)(threads / 32) * a.spw * 16;
 }

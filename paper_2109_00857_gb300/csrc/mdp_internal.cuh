@@ -172,6 +172,32 @@ struct SolveArgs {
   int32_t A, A_pad, spw, N, nbins;
   double tol;
 };
+// batched solve (FP32): one Jacobi sweep over many models per launch
+struct BatchSolveItem {
+  SolveArgs a;                // the model (R of the objective being solved)
+  float *Va, *Vb;             // V ping-pong (Va = the caller's output)
+  int16_t *policy;
+  unsigned long long *res;    // [max_sweeps] residual bits, zeroed per run
+  double *stats;              // [4] sweeps, residual
+  int max_sweeps;
+};
+struct BatchCta {
+  int item;
+  int64_t sl_lo, sl_hi;
+};
+cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm);
+cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, const BatchCta *ctas_d, int n_ctas, int k,
+                                 int stage_bytes, cudaStream_t st);
+cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st);
+// batched build (FP32): one persistent warp launch over every model's slices
+// (prefix[m] = first global slice of model m, prefix[n] = total), then the
+// full-window CTA kernel over every model's deferred slices
+cudaError_t launch_build_warp_batch(const BuildArgs *items_d, const int64_t *prefix_d, int n,
+                                    unsigned long long *work_d, int cap_bins, int kmax, int spw_all,
+                                    cudaStream_t st);
+cudaError_t launch_build_fp32_batch(const BuildArgs *items_d, int n, size_t smem, int threads,
+                                    cudaStream_t st);
+size_t fp32_smem_bytes(const BuildArgs &a, int threads);
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st);
 cudaError_t launch_layered(const SolveArgs &a, int precision, int nt, void *V, int16_t *policy,
@@ -186,6 +212,19 @@ int num_sms();
 // (kernel, device).  Launches then pass their own size; the limit is never
 // lowered, so concurrent launches with different sizes cannot race on it.
 cudaError_t allow_max_smem(const void *func);
+
+// Hand-over of a prepared (not yet built) model to the batched build.
+struct BuildHook {
+  uint64_t pool_cols = 0;     // in: entry-pool capacity in columns (0 = default guess); out: used
+  BuildArgs args;             // out: kernel arguments
+  void *Yown = nullptr;       // out: coefficient table owned by the caller now
+  double *sigma_d = nullptr;  // out: device sigma (owned by the caller now)
+  uint32_t *defer = nullptr;  // out: deferred-slice list (owned by the caller now)
+  int threads = 256;          // out: CTA size of the full-window kernel
+};
+mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
+                      int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,
+                      void *stream, mdp_model *out, BuildHook *hook);
 
 // Frees a model's device memory in the order of `st` (no device-wide sync):
 // for callers that know the model's work was issued on that stream.

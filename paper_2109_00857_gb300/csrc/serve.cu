@@ -409,14 +409,3 @@ extern "C" mdp_status mdp_serve_destroy(mdp_server S) {
   return MDP_OK;
 }
 
-// ------------------------------------------------------------- batching --
-static mdp_status batch_not_built(const char *what) {
-  set_error(std::string(what) + ": not available in this build");
-  return MDP_ERR_ARG;
-}
-extern "C" mdp_status mdp_batch_create(const mdp_batch_item *, int32_t, double, mdp_batch *out) {
-  if (out) *out = nullptr;
-  return batch_not_built("mdp_batch_create");
-}
-extern "C" mdp_status mdp_batch_run(mdp_batch, void *, int32_t *, double *) { return batch_not_built("mdp_batch_run"); }
-extern "C" void mdp_batch_free(mdp_batch) {}

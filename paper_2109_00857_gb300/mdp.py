@@ -368,3 +368,49 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------- batching --
+class Batch:
+    """Many MDPs built and solved together (mdp_batch_*): one persistent build
+    launch, one launch per Jacobi sweep over all items, captured in a CUDA
+    graph on the first run.  Keeps the DeviceEnvs and outputs alive."""
+
+    def __init__(self, denvs, objectives=None, tol: float = 0.0):
+        import torch
+        self.denvs = list(denvs)
+        n = len(self.denvs)
+        arr = (MdpBatchItem * n)()
+        self.V, self.policy = [], []
+        for i, d in enumerate(self.denvs):
+            it = arr[i]
+            it.env, it.grid, it.actions = d.c_env(), d.c_grid(), d.c_actions()
+            it.N, it.subgrid_L = d.env.N, d.env.L
+            it.objective = (objectives[i] if objectives is not None else d.env.objectives[0])
+            V = torch.empty(d.env.nS + 1, dtype=torch.float32, device="cuda")
+            pi = torch.empty(d.env.nS, dtype=torch.int16, device="cuda")
+            self.V.append(V)
+            self.policy.append(pi)
+            it.V, it.policy = _ptr(V), _ptr(pi)
+        h = P()
+        _check(load().mdp_batch_create(arr, n, float(tol), C.byref(h)), "mdp_batch_create")
+        self.handle = h.value
+        self.n = n
+
+    def run(self, stream=None):
+        """Returns (sweeps per item, device ms of the run)."""
+        sw = (C.c_int32 * self.n)()
+        ms = C.c_double()
+        _check(load().mdp_batch_run(self.handle, _stream(stream), sw, C.byref(ms)), "mdp_batch_run")
+        return list(sw), ms.value
+
+    def close(self):
+        if self.handle:
+            load().mdp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
