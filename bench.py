@@ -192,13 +192,138 @@ def aggregate(t_ms, samples, backups, world, device):
     return float(tmax[0]), float(tsum[0]), float(tsum[1])
 
 
+def run_batch(args):
+    """64 uneven MDPs: one batched run (persistent build launch + batched
+    sweeps, CUDA graph) against the same 64 built and solved one after another
+    with the plain calls."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import inputs, mdp
+    mdp.load()
+    envs = [inputs.batch_member(i) for i in range(64)]
+    denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
+    b = mdp.Batch(denvs, tol=0.0)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sweeps, ms = b.run()
+        times.append(time.perf_counter() - t0)
+    batch_s = statistics.median(times)
+    samples = sum(e.samples() - e.N * e.A * e.Nc for e in envs)   # the last layer needs no sampling
+    # the plain path: build + solve each member in turn
+    stream = torch.cuda.current_stream()
+    def plain():
+        for d, e in zip(denvs, envs):
+            m = mdp.mdp_build(d, objs=(e.objectives[0],))
+            mdp.mdp_solve(m, 0, tol=0.0)
+            m.free()
+    plain()
+    torch.cuda.synchronize()
+    pt = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        plain()
+        torch.cuda.synchronize()
+        pt.append(time.perf_counter() - t0)
+    plain_s = statistics.median(pt)
+    line = {"metric": "batched build+solve, solves/s (64 uneven MDPs)", "value": 64 / batch_s,
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": batch_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 batch members: side U{40..160}, nt U{20..80}, K U{2..6}, "
+                                   "N U{500..2000}, A in {16, 32}", "states": sum(e.nS for e in envs)},
+            "transitions_per_s": samples / batch_s, "graph_ms_device": ms,
+            "sequential_plain": {"solves_per_s": 64 / plain_s, "ms": plain_s * 1e3},
+            "speedup_vs_sequential": plain_s / batch_s, "sweeps_max": max(sweeps)}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+def run_serve(args):
+    """Poisson replanning requests against the server (8 slots, 120 GB budget)
+    and against one-at-a-time processing (1 slot), same request stream."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import inputs, mdp
+    mdp.load()
+    rng = np.random.default_rng(5500)
+    sides = [30, 48, 66, 84, 102, 120]
+    envs = []
+    for k, side in enumerate(sides):
+        nt = int(rng.integers(20, 61))
+        K = int(rng.integers(1, 7))
+        envs.append(inputs.make_env(nx=side, ny=side, nt=nt, K=K, N=1000, L=21,
+                                    sigma=tuple(0.3 * 2.0 ** (-q / 2.0) for q in range(K)), seed=5501 + k,
+                                    amplitude=2.0, n_headings=16, n_speeds=1 + (k % 2), obstacle="squares",
+                                    square=max(4, side // 10), with_gbar=True))
+    denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
+
+    def requests(rate, seconds, seed):
+        r = np.random.default_rng(seed)
+        t, out = 0.0, []
+        while True:
+            t += r.exponential(1.0 / rate)
+            if t > seconds:
+                return out
+            k = int(r.integers(0, len(envs)))
+            side = sides[k]
+            out.append((t, k, dict(start=(int(r.integers(0, side)), int(r.integers(0, side))),
+                                   target=(int(r.integers(0, side - 2)), int(r.integers(0, side - 2))),
+                                   sigma_scale=float(r.uniform(0.5, 1.5)), seed=int(r.integers(1, 1 << 30)),
+                                   N=int(r.integers(500, 2001)), objective=int(r.integers(0, 3)))))
+
+    def run(slots, reqs):
+        srv = mdp.Server(120 << 30, slots)
+        ids = [srv.register(d) for d in denvs]
+        w = srv.submit(ids[0], start=(1, 1), target=(5, 5), N=200)   # warm-up
+        srv.poll(w, timeout_ms=120000)
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, k, kw) in reqs:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(srv.submit(ids[k], **kw))
+        lat = []
+        for t in tickets:
+            res, _, _ = srv.poll(t, timeout_ms=600000)
+            assert res.status == 0
+            lat.append(res.latency_ms)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "solves_per_s": len(lat) / wall, "requests": len(lat), "wall_s": wall}
+
+    rows = []
+    for rate in [float(x) for x in args.serve_rates.split(",")]:
+        reqs = requests(rate, args.serve_seconds, int(rate) + 1)
+        served = run(8, reqs)
+        single = run(1, reqs)
+        rows.append({"rate_per_s": rate, "served_8_slots": served, "one_at_a_time": single})
+    top = rows[-1]["served_8_slots"]
+    line = {"metric": "replan p50/p99 ms", "value": top["p99_ms"], "unit": "ms (p99 at the highest rate)",
+            "n_gpus": 1, "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Poisson replanning requests, {args.serve_seconds:.0f} s per rate, "
+                                   "grids 30..120, nt 20..60, K<=6, N 500..2000, sigma x0.5..1.5, "
+                                   "120 GB budget"},
+            "rates": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="large", choices=["tiny", "energy", "large"])
+    ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-rates", default="20,50,100,200")
     ap.add_argument("--solve", default="jacobi", choices=["jacobi", "layered"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -210,6 +335,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "batch":
+        run_batch(args)
+        return
+    if args.config == "serve":
+        run_serve(args)
         return
 
     import torch
