@@ -113,6 +113,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // Bounded wait: gives up after ~2 s of clock cycles so a lost arrival can
 // never hang the GPU; the caller reports the timeout through the error word.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;   // usual case: the data is there
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > 4000000000LL) return false;
@@ -179,8 +180,8 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
   const RT *Rg = static_cast<const RT *>(a.R);
   uint32_t m_off = 0, m_w = 0;   // lane l: metadata of my slice 32*(j/32) + l
 
-  // issue(j): copy my j-th slice into stage j % kDepth (whole warp calls it)
-  auto issue = [&](int j) {
+  // issue(j, st): copy my j-th slice into stage st = j % kDepth (whole warp calls it)
+  auto issue = [&](int j, int st) {
     if ((j & 31) == 0) {
       const int jj = j + lane;
       if (jj < n_mine) {
@@ -192,7 +193,6 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
     const uint32_t off = __shfl_sync(0xffffffffu, m_off, j & 31);
     const uint32_t W = __shfl_sync(0xffffffffu, m_w, j & 31);
     if (lane == 0) {
-      const int st = j % kDepth;
       wst_s[warp * kDepth + st] = (int)W;
       const uint32_t sbase = ring0 + (uint32_t)(st * pr.stage_bytes);
       const uint32_t fb = bar0 + 8u * (uint32_t)st;
@@ -210,10 +210,12 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
   const RT invN = (RT)1 / (RT)a.N;
   float rf = 0.f;      // FP32 residual
   double r = 0.0;      // FP64 residual
-  for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j);
+  for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j, j);
   int st = 0;
   uint32_t phase = 0;
-  for (int j = 0; j < n_mine; ++j) {
+  int s = sl0 * a.spw + q;                      // state of this lane's row in my j-th slice
+  const int s_step = kWarps * a.spw;
+  for (int j = 0; j < n_mine; ++j, s += s_step) {
     if (!mbar_wait(bar0 + 8u * (uint32_t)st, phase)) {
       if (lane == 0) atomicOr(a.err, 1);
       // drain: wait (bounded) for the copies still in flight into my stages
@@ -223,7 +225,6 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
     }
     const unsigned char *sb = myring + st * pr.stage_bytes;
     const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb) + lane;
-    const int s = (sl0 + j * kWarps) * a.spw + q;
     const bool valid = s >= s_lo && s < s_hi && act < a.A;
     const RT Rv = reinterpret_cast<const RT *>(sb + roff)[lane];
     const int W = wst_s[warp * kDepth + st];
@@ -237,7 +238,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
       acc.add(w >> 16, Vn[(int)(int16_t)(w & 0xFFFFu)], a.N);
     }
     __syncwarp();
-    if (j + kDepth < n_mine) issue(j + kDepth);   // refill the stage just read
+    if (j + kDepth < n_mine) issue(j + kDepth, st);   // refill the stage just read
     if (++st == kDepth) {
       st = 0;
       phase ^= 1u;
@@ -438,16 +439,18 @@ cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, voi
 
 template <typename RT>
 static cudaError_t layered_t(const SolveArgs &a, int nt, RT *V, int16_t *policy, cudaStream_t st) {
+  PipeRange pr0;
+  size_t smem = 0;
+  int blocks = 1;
+  // every layer has the same number of slices (up to one straddling slice)
+  cudaError_t e = pipe_config<RT>(a, (a.Nc + a.spw - 1) / a.spw + 1, &pr0, &smem, &blocks);
+  if (e != cudaSuccess) return e;
   for (int t = nt - 1; t >= 0; --t) {
-    PipeRange pr;
+    PipeRange pr = pr0;
     pr.s_lo = (int64_t)t * a.Nc;
     pr.s_hi = pr.s_lo + a.Nc;
     pr.sl_lo = pr.s_lo / a.spw;
     pr.sl_hi = (pr.s_hi + a.spw - 1) / a.spw;
-    size_t smem = 0;
-    int blocks = 1;
-    cudaError_t e = pipe_config<RT>(a, pr.sl_hi - pr.sl_lo, &pr, &smem, &blocks);
-    if (e != cudaSuccess) return e;
     bellman_kernel<RT><<<blocks, 32 * kWarps, smem, st>>>(a, V, V, policy, nullptr, 0, pr);
   }
   return cudaGetLastError();
