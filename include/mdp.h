@@ -188,6 +188,22 @@ typedef struct {
 mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol, int32_t max_sweeps,
                      void *V, int16_t *policy, void *stream, mdp_solve_stats *stats);
 
+/* Value iteration for n (1..3) objectives of one model at once (Sec. II-B
+ * backup per objective; Sec. III-D solves each objective's MDP on the same
+ * P).  Each sweep streams the transition slices once for all n objectives;
+ * every objective keeps its own R, V, policy and residual, so objective o's
+ * V, policy, sweeps and residual equal those of mdp_solve(m, objs[o], ...)
+ * with the same method, tol and max_sweeps bit for bit (an objective that
+ * met tol stops updating while the others continue).
+ * objs: host [n] objective slots (repeats allowed); V, policy: host arrays of
+ * n device pointers laid out as in mdp_solve; stats: host [n] or NULL.
+ * solve_ms is the device time of the whole fused solve for every entry.
+ * Errors: MDP_ERR_ARG for n outside 1..3, a NULL pointer or a slot out of
+ * range; otherwise as mdp_solve.  Synchronises `stream` once. */
+mdp_status mdp_solve_multi(mdp_model m, int32_t n, const int32_t *objs, int32_t method, double tol,
+                           int32_t max_sweeps, void *const *V, int16_t *const *policy, void *stream,
+                           mdp_solve_stats *stats);
+
 /* The same Jacobi value iteration as mdp_solve (method MDP_SOLVE_JACOBI),
  * for callers that may not allocate device memory once they are running:
  * a real-time replanning loop that must not block or fragment its memory

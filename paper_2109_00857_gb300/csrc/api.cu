@@ -527,11 +527,18 @@ extern "C" mdp_status mdp_export_csr(mdp_model m, int32_t obj, int64_t *rowptr, 
   return MDP_OK;
 }
 
-extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol,
-                                int32_t max_sweeps, void *V, int16_t *policy, void *stream,
-                                mdp_solve_stats *stats) {
-  if (!m || !V || !policy) return arg_fail("NULL model, V or policy");
-  if (obj < 0 || obj >= m->n_obj) return arg_fail("objective slot out of range");
+// Value iteration for n objectives on one model: the Bellman kernels stream
+// P once per sweep for all of them (mdp_solve is the n = 1 case).
+static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_t method, double tol,
+                             int32_t max_sweeps, void *const *V, int16_t *const *policy, void *stream,
+                             mdp_solve_stats *stats) {
+  if (!m) return arg_fail("NULL model");
+  if (n < 1 || n > 3) return arg_fail("n must be 1, 2 or 3");
+  if (!objs || !V || !policy) return arg_fail("NULL objs, V or policy");
+  for (int o = 0; o < n; ++o) {
+    if (!V[o] || !policy[o]) return arg_fail("NULL V or policy");
+    if (objs[o] < 0 || objs[o] >= m->n_obj) return arg_fail("objective slot out of range");
+  }
   if (method != MDP_SOLVE_JACOBI && method != MDP_SOLVE_LAYERED) return arg_fail("method");
   if (!(tol >= 0) && !(tol < 0)) return arg_fail("tol is NaN");
   if (max_sweeps < 0) return arg_fail("max_sweeps must be >= 0");
@@ -546,16 +553,36 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
     return MDP_ERR_CUDA;
   }
   if (m->nS + m->Nc >= ((int64_t)1 << 31)) return arg_fail("more than 2^31 states is not supported by the solver");
-  if (method == MDP_SOLVE_JACOBI && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
+  const bool jac = method == MDP_SOLVE_JACOBI;
+  // Jacobi partners: the model's cached buffer for the first objective,
+  // stream-ordered scratch for the others
+  if (jac && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
+  void *extra = nullptr;
+  if (jac && n > 1) MDP_CUDA_TRY(dev_alloc(&extra, vbytes * (size_t)(n - 1), st));
+  const size_t blk = 4 + (size_t)max_sweeps;
   double *sd = nullptr;
-  MDP_CUDA_TRY(dev_alloc((void **)&sd, sizeof(double) * (4 + (size_t)max_sweeps), st));
-  MDP_CUDA_TRY(cudaMemsetAsync(sd, 0, sizeof(double) * 4, st));
-  MDP_CUDA_TRY(cudaMemsetAsync(V, 0, vbytes, st));
-  if (method == MDP_SOLVE_JACOBI) MDP_CUDA_TRY(cudaMemsetAsync(m->Vtmp, 0, vbytes, st));
+  cudaError_t ce = dev_alloc((void **)&sd, sizeof(double) * blk * (size_t)n, st);
+  if (ce != cudaSuccess) {
+    if (extra) dev_free(extra, st);
+    return cuda_fail(ce, "dev_alloc");
+  }
+  SolveIO io;
+  io.n = n;
+  for (int o = 0; o < n; ++o) {
+    io.R[o] = static_cast<const char *>(m->R) + fsz * (size_t)objs[o] * m->rows_pad;
+    io.V[o] = V[o];
+    io.Vtmp[o] = !jac ? nullptr : (o == 0 ? m->Vtmp : static_cast<char *>(extra) + vbytes * (size_t)(o - 1));
+    io.policy[o] = policy[o];
+  }
+  for (int o = 0; o < n && ce == cudaSuccess; ++o) {
+    ce = cudaMemsetAsync(sd + o * blk, 0, sizeof(double) * 4, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(io.V[o], 0, vbytes, st);
+    if (ce == cudaSuccess && jac) ce = cudaMemsetAsync(io.Vtmp[o], 0, vbytes, st);
+  }
   SolveArgs a;
   a.pool = m->pool; a.slice_off = m->slice_off; a.slice_w = m->slice_w; a.nnz = m->nnz;
   a.wcap = std::max(1, m->max_row_nnz);
-  a.R = static_cast<const char *>(m->R) + fsz * (size_t)obj * m->rows_pad;
+  a.R = io.R[0];
   a.cls = m->cls; a.delta = m->delta;
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;
   a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
@@ -564,40 +591,50 @@ extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  cudaError_t ce;
-  if (method == MDP_SOLVE_JACOBI) ce = launch_jacobi(a, m->precision, max_sweeps, V, m->Vtmp, policy, sd, st);
-  else ce = launch_layered(a, m->precision, m->nt, V, policy, sd, st);
+  if (ce == cudaSuccess) {
+    if (jac) ce = launch_jacobi_multi(a, m->precision, max_sweeps, io, sd, st);
+    else ce = launch_layered_multi(a, m->precision, m->nt, io, st);
+  }
   cudaEventRecord(e1, st);
-  double hs[2] = {0, 0};
-  double hs3[3] = {0, 0, 0};
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hs3, sd, sizeof(hs3), cudaMemcpyDeviceToHost, st);
+  double hs[3][3] = {};
+  for (int o = 0; o < n && ce == cudaSuccess; ++o)
+    ce = cudaMemcpyAsync(hs[o], sd + o * blk, sizeof(hs[o]), cudaMemcpyDeviceToHost, st);
   dev_free(sd, st);
+  if (extra) dev_free(extra, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   float ms = 0.f;
   if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (ce != cudaSuccess) return cuda_fail(ce, "mdp_solve");
-  hs[0] = hs3[0];
-  hs[1] = hs3[1];
   int errw = 0;
-  memcpy(&errw, &hs3[2], sizeof(int));
+  memcpy(&errw, &hs[0][2], sizeof(int));
   if (errw) {
     set_error("a bounded device wait expired in the Bellman pipeline");
     return MDP_ERR_TIMEOUT;
   }
   if (stats) {
-    if (method == MDP_SOLVE_JACOBI) {
-      stats->sweeps = (int32_t)hs[0];
-      stats->residual = hs[1];
-    } else {
-      stats->sweeps = 1;
-      stats->residual = 0.0;
+    for (int o = 0; o < n; ++o) {
+      stats[o].sweeps = jac ? (int32_t)hs[o][0] : 1;
+      stats[o].residual = jac ? hs[o][1] : 0.0;
+      stats[o].solve_ms = ms;
+      stats[o].backups = (int64_t)stats[o].sweeps * m->nS * m->A;
     }
-    stats->solve_ms = ms;
-    stats->backups = (int64_t)stats->sweeps * m->nS * m->A;
   }
   return MDP_OK;
+}
+
+extern "C" mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol,
+                                int32_t max_sweeps, void *V, int16_t *policy, void *stream,
+                                mdp_solve_stats *stats) {
+  if (!m || !V || !policy) return arg_fail("NULL model, V or policy");
+  return solve_impl(m, 1, &obj, method, tol, max_sweeps, &V, &policy, stream, stats);
+}
+
+extern "C" mdp_status mdp_solve_multi(mdp_model m, int32_t n, const int32_t *objs, int32_t method,
+                                      double tol, int32_t max_sweeps, void *const *V,
+                                      int16_t *const *policy, void *stream, mdp_solve_stats *stats) {
+  return solve_impl(m, n, objs, method, tol, max_sweeps, V, policy, stream, stats);
 }
 
 extern "C" void mdp_model_free(mdp_model m) {

@@ -152,12 +152,31 @@ static int stage_bytes_for(int wcap, size_t rsz) {
 // res != nullptr: Jacobi sweep k (exits at once if sweep k-1 met the
 // tolerance) with the residual reduced into res[k-1].
 // One CTA, slices [b_lo, b_hi) of one model (all threads call it).
-template <typename RT>
-__device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, RT *Vout, int16_t *policy,
-                                             unsigned long long *res, int k, int64_t b_lo, int64_t b_hi,
-                                             const PipeRange &pr, unsigned char *sm, double *wmax,
-                                             int *wst_s) {
-  if (res && k > 1 && __longlong_as_double((long long)res[k - 2]) <= a.tol) return;
+// Per-objective operands of one Bellman launch.  NO objectives share the
+// streamed transition slices (each slice is copied once per sweep), each
+// with its own R, value buffers, policy and residual slots; res[o] ==
+// nullptr marks a layered pass (no residual, no early exit).
+template <typename RT, int NO>
+struct VSet {
+  const RT *R[NO];
+  const RT *in[NO];
+  RT *out[NO];
+  int16_t *pol[NO];
+  unsigned long long *res[NO];
+};
+
+template <typename RT, int NO>
+__device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
+                                             int64_t b_hi, const PipeRange &pr, unsigned char *sm,
+                                             double *wmax, int *wst_s) {
+  // objectives whose previous sweep met the tolerance are finished
+  unsigned live = (1u << NO) - 1u;
+  if (k > 1) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (v.res[o] && __longlong_as_double((long long)v.res[o][k - 2]) <= a.tol) live &= ~(1u << o);
+  }
+  if (!live) return;
   if (*(volatile int *)a.err) return;   // an earlier launch of this solve timed out
   uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // [kWarps][kDepth]
   unsigned char *ring = sm + 256;
@@ -168,16 +187,14 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
   if (tid < kWarps * kDepth) mbar_init(smem_u32(full + tid), 1);
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  const size_t rsz = sizeof(RT);
+  constexpr uint32_t rbytes = 32u * (uint32_t)sizeof(RT);   // one slice's R of one objective
   const int roff = a.wcap * 128;          // R block offset inside a stage
   unsigned char *myring = ring + (size_t)warp * kDepth * pr.stage_bytes;
-  uint64_t *myfull = full + warp * kDepth;
 
   // 32-bit slice/state indices (the host guarantees |S| + Nc < 2^31)
   const int n_mine = (n_local > warp) ? (int)((n_local - warp + kWarps - 1) / kWarps) : 0;
   const int sl0 = (int)b_lo + warp;                       // my j-th slice: sl0 + j*kWarps
-  const uint32_t ring0 = smem_u32(myring), bar0 = smem_u32(myfull);
-  const RT *Rg = static_cast<const RT *>(a.R);
+  const uint32_t ring0 = smem_u32(myring), bar0 = smem_u32(full + warp * kDepth);
   uint32_t m_off = 0, m_w = 0;   // lane l: metadata of my slice 32*(j/32) + l
 
   // issue(j, st): copy my j-th slice into stage st = j % kDepth (whole warp calls it)
@@ -196,10 +213,12 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
       wst_s[warp * kDepth + st] = (int)W;
       const uint32_t sbase = ring0 + (uint32_t)(st * pr.stage_bytes);
       const uint32_t fb = bar0 + 8u * (uint32_t)st;
+      const size_t sl = (size_t)(sl0 + j * kWarps);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage
-      mbar_expect_tx(fb, W * 128u + 32u * (uint32_t)rsz);
+      mbar_expect_tx(fb, W * 128u + NO * rbytes);
       if (W) bulk_g2s(sbase, a.pool + (size_t)off * 32, W * 128u, fb);
-      bulk_g2s(sbase + (uint32_t)roff, Rg + (size_t)(sl0 + j * kWarps) * 32, 32u * (uint32_t)rsz, fb);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) bulk_g2s(sbase + (uint32_t)roff + o * rbytes, v.R[o] + sl * 32, rbytes, fb);
     }
     __syncwarp();
   };
@@ -208,8 +227,13 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
   const int nS = (int)a.nS, Nc = (int)a.Nc;
   const int s_lo = (int)pr.s_lo, s_hi = (int)pr.s_hi;
   const RT invN = (RT)1 / (RT)a.N;
-  float rf = 0.f;      // FP32 residual
-  double r = 0.0;      // FP64 residual
+  float rf[NO];      // FP32 residuals
+  double r[NO];      // FP64 residuals
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    rf[o] = 0.f;
+    r[o] = 0.0;
+  }
   for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j, j);
   int st = 0;
   uint32_t phase = 0;
@@ -226,16 +250,23 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
     const unsigned char *sb = myring + st * pr.stage_bytes;
     const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb) + lane;
     const bool valid = s >= s_lo && s < s_hi && act < a.A;
-    const RT Rv = reinterpret_cast<const RT *>(sb + roff)[lane];
+    RT Rv[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) Rv[o] = reinterpret_cast<const RT *>(sb + roff + o * rbytes)[lane];
     const int W = wst_s[warp * kDepth + st];
-    Acc<RT> acc;
+    Acc<RT> acc[NO];
     // successor layer base of this state; rows without successors (last
     // layer, padding lanes) hold only padding words and read V[|S|] = 0
-    const RT *Vn = Vin + ((s + Nc <= nS) ? s + Nc : nS);
+    const int sn = (s + Nc <= nS) ? s + Nc : nS;
+    const RT *Vn[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) Vn[o] = v.in[o] + sn;
 #pragma unroll 4
     for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
       const uint32_t w = ent[kk * 32];
-      acc.add(w >> 16, Vn[(int)(int16_t)(w & 0xFFFFu)], a.N);
+      const int off = (int)(int16_t)(w & 0xFFFFu);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, Vn[o][off], a.N);
     }
     __syncwarp();
     if (j + kDepth < n_mine) issue(j + kDepth, st);   // refill the stage just read
@@ -243,59 +274,66 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const RT *Vin, 
       st = 0;
       phase ^= 1u;
     }
-    RT qv = valid ? acc.q(Rv, invN) : -(RT)INFINITY;
-    int qa = act;
-    if (sizeof(RT) == 4 && a.A_pad == 32) {
-      // one state per warp: order-preserving integer key, warp max in one
-      // redux, lowest lane (= lowest action) among the maxima by ballot
-      const uint32_t bits = __float_as_uint((float)qv + 0.0f);   // -0 keys like +0
-      const uint32_t key = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
-      const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
-      qa = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
-      qv = __shfl_sync(0xffffffffu, qv, qa);
-    } else {
-      for (int o = 1; o < a.A_pad; o <<= 1) {
-        const RT oq = __shfl_xor_sync(0xffffffffu, qv, o);
-        const int oa = __shfl_xor_sync(0xffffffffu, qa, o);
-        if (oq > qv || (oq == qv && oa < qa)) {
-          qv = oq;
-          qa = oa;
+    const bool head = act == 0 && s >= s_lo && s < s_hi;   // the lane that writes state s
+    const bool term = head && __ldg(a.cls + s) != CLS_FREE;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      RT qv = valid ? acc[o].q(Rv[o], invN) : -(RT)INFINITY;
+      int qa = act;
+      if (sizeof(RT) == 4 && a.A_pad == 32) {
+        // one state per warp: order-preserving integer key, warp max in one
+        // redux, lowest lane (= lowest action) among the maxima by ballot
+        const uint32_t bits = __float_as_uint((float)qv + 0.0f);   // -0 keys like +0
+        const uint32_t key = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+        qa = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
+        qv = __shfl_sync(0xffffffffu, qv, qa);
+      } else {
+        for (int m = 1; m < a.A_pad; m <<= 1) {
+          const RT oq = __shfl_xor_sync(0xffffffffu, qv, m);
+          const int oa = __shfl_xor_sync(0xffffffffu, qa, m);
+          if (oq > qv || (oq == qv && oa < qa)) {
+            qv = oq;
+            qa = oa;
+          }
         }
       }
-    }
-    if (act == 0 && s >= s_lo && s < s_hi) {
-      const RT old = Vin[s];
-      Vout[s] = qv;
-      policy[s] = (__ldg(a.cls + s) != CLS_FREE) ? (int16_t)-1 : (int16_t)qa;
-      if constexpr (sizeof(RT) == 4) rf = fmaxf(rf, fabsf(qv - old));
-      else r = fmax(r, fabs(qv - old));
+      if (head && ((live >> o) & 1u)) {
+        const RT old = v.in[o][s];
+        v.out[o][s] = qv;
+        v.pol[o][s] = term ? (int16_t)-1 : (int16_t)qa;
+        if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv - old));
+        else r[o] = fmax(r[o], fabs(qv - old));
+      }
     }
   }
-  if constexpr (sizeof(RT) == 4) r = (double)rf;
-  if (res) {
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-    if (lane == 0) wmax[warp] = r;
+  if (v.res[0]) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      double ro = (sizeof(RT) == 4) ? (double)rf[o] : r[o];
+      for (int m = 16; m > 0; m >>= 1) ro = fmax(ro, __shfl_xor_sync(0xffffffffu, ro, m));
+      if (lane == 0) wmax[warp * NO + o] = ro;
+    }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < NO) {
       double m = 0.0;
-      for (int i = 0; i < kWarps; ++i) m = fmax(m, wmax[i]);
-      if (m > 0.0) atomicMax(&res[k - 1], (unsigned long long)__double_as_longlong(m));
+      for (int i = 0; i < kWarps; ++i) m = fmax(m, wmax[i * NO + tid]);
+      if (m > 0.0) atomicMax(&v.res[tid][k - 1], (unsigned long long)__double_as_longlong(m));
     }
   }
 }
 
-template <typename RT>
-__global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, const RT *Vin, RT *Vout,
-                                                              int16_t *policy, unsigned long long *res, int k,
+template <typename RT, int NO>
+__global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, VSet<RT, NO> v, int k,
                                                               PipeRange pr) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ double wmax[kWarps];
+  __shared__ double wmax[kWarps * NO];
   __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
   const int64_t total = pr.sl_hi - pr.sl_lo;
   const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
   const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
   const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
-  bellman_body<RT>(a, Vin, Vout, policy, res, k, b_lo, b_hi, pr, sm, wmax, wst_s);
+  bellman_body<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
 }
 
 // Batched Jacobi sweep k over many models: CTA b works on ctas[b] (one
@@ -316,9 +354,13 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   pr.s_hi = it.a.nS;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
-  const float *vin = (k & 1) ? it.Va : it.Vb;
-  float *vout = (k & 1) ? it.Vb : it.Va;
-  bellman_body<float>(it.a, vin, vout, it.policy, it.res, k, c.sl_lo, c.sl_hi, pr, sm, wmax, wst_s);
+  VSet<float, 1> v;
+  v.R[0] = static_cast<const float *>(it.a.R);
+  v.in[0] = (k & 1) ? it.Va : it.Vb;
+  v.out[0] = (k & 1) ? it.Vb : it.Va;
+  v.pol[0] = it.policy;
+  v.res[0] = it.res;
+  bellman_body<float, 1>(it.a, v, k, c.sl_lo, c.sl_hi, pr, sm, wmax, wst_s);
 }
 
 // Per model (one block each): sweeps and residual, final iterate into Va.
@@ -381,16 +423,16 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
     Va[i] = Vb[i];
 }
 
-template <typename RT>
+template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
-  pr->stage_bytes = stage_bytes_for(a.wcap, sizeof(RT));
+  pr->stage_bytes = stage_bytes_for(a.wcap, NO * sizeof(RT));
   pr->dtab_smem = 0;
   *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
   if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = allow_max_smem((const void *)bellman_kernel<RT>);
+  cudaError_t e = allow_max_smem((const void *)bellman_kernel<RT, NO>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<RT>, 32 * kWarps, *smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<RT, NO>, 32 * kWarps, *smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t b = (int64_t)num_sms() * per_sm;
@@ -401,66 +443,119 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
   return cudaSuccess;
 }
 
-template <typename RT>
-static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, RT *Va, RT *Vb, int16_t *policy,
-                            double *stats_d, cudaStream_t st) {
-  // residual slots live after the 4 stats doubles
-  unsigned long long *res = reinterpret_cast<unsigned long long *>(stats_d + 4);
-  cudaError_t e = cudaMemsetAsync(res, 0, sizeof(unsigned long long) * (size_t)max_sweeps, st);
-  if (e != cudaSuccess) return e;
+// Objective o's status block: stats_d + o*(4 + max_sweeps) holds sweeps,
+// residual, (objective 0: the error word), spare, then one residual slot
+// per sweep.
+template <typename RT, int NO>
+static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, const SolveIO &io, double *stats_d,
+                            cudaStream_t st) {
+  const size_t blk = 4 + (size_t)max_sweeps;
+  VSet<RT, NO> odd, even;   // sweep k reads Va when k is odd, Vb when even
+  for (int o = 0; o < NO; ++o) {
+    unsigned long long *res = reinterpret_cast<unsigned long long *>(stats_d + o * blk + 4);
+    cudaError_t e = cudaMemsetAsync(res, 0, sizeof(unsigned long long) * (size_t)max_sweeps, st);
+    if (e != cudaSuccess) return e;
+    odd.R[o] = even.R[o] = static_cast<const RT *>(io.R[o]);
+    RT *va = static_cast<RT *>(io.V[o]), *vb = static_cast<RT *>(io.Vtmp[o]);
+    odd.in[o] = va;
+    odd.out[o] = vb;
+    even.in[o] = vb;
+    even.out[o] = va;
+    odd.pol[o] = even.pol[o] = io.policy[o];
+    odd.res[o] = even.res[o] = res;
+  }
   PipeRange pr;
   size_t smem = 0;
   int blocks = 1;
-  e = pipe_config<RT>(a, a.n_slices, &pr, &smem, &blocks);
+  cudaError_t e = pipe_config<RT, NO>(a, a.n_slices, &pr, &smem, &blocks);
   if (e != cudaSuccess) return e;
   pr.sl_lo = 0;
   pr.sl_hi = a.n_slices;
   pr.s_lo = 0;
   pr.s_hi = a.nS;
-  for (int k = 1; k <= max_sweeps; ++k) {
-    const RT *vin = (k & 1) ? Va : Vb;
-    RT *vout = (k & 1) ? Vb : Va;
-    bellman_kernel<RT><<<blocks, 32 * kWarps, smem, st>>>(a, vin, vout, policy, res, k, pr);
-  }
+  for (int k = 1; k <= max_sweeps; ++k)
+    bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, (k & 1) ? odd : even, k, pr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t fb = (a.nS + 1 + 255) / 256;
   if (fb > 1024) fb = 1024;
-  finalize_kernel<RT><<<(unsigned)fb, 256, 0, st>>>(res, max_sweeps, a.tol, Va, Vb, a.nS + 1, stats_d);
+  for (int o = 0; o < NO; ++o) {
+    finalize_kernel<RT><<<(unsigned)fb, 256, 0, st>>>(odd.res[o], max_sweeps, a.tol, static_cast<RT *>(io.V[o]),
+                                                       static_cast<const RT *>(io.Vtmp[o]), a.nS + 1,
+                                                       stats_d + o * blk);
+  }
   return cudaGetLastError();
+}
+
+template <typename RT>
+static cudaError_t jacobi_n(const SolveArgs &a, int max_sweeps, const SolveIO &io, double *stats_d,
+                            cudaStream_t st) {
+  switch (io.n) {
+    case 1: return jacobi_t<RT, 1>(a, max_sweeps, io, stats_d, st);
+    case 2: return jacobi_t<RT, 2>(a, max_sweeps, io, stats_d, st);
+    case 3: return jacobi_t<RT, 3>(a, max_sweeps, io, stats_d, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_jacobi_multi(const SolveArgs &a, int precision, int max_sweeps, const SolveIO &io,
+                                double *stats_d, cudaStream_t st) {
+  if (precision == MDP_FP64_CHECK) return jacobi_n<double>(a, max_sweeps, io, stats_d, st);
+  return jacobi_n<float>(a, max_sweeps, io, stats_d, st);
 }
 
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st) {
-  if (precision == MDP_FP64_CHECK)
-    return jacobi_t<double>(a, max_sweeps, (double *)Va, (double *)Vb, policy, stats_d, st);
-  return jacobi_t<float>(a, max_sweeps, (float *)Va, (float *)Vb, policy, stats_d, st);
+  SolveIO io;
+  io.n = 1;
+  io.R[0] = a.R;
+  io.V[0] = Va;
+  io.Vtmp[0] = Vb;
+  io.policy[0] = policy;
+  return launch_jacobi_multi(a, precision, max_sweeps, io, stats_d, st);
 }
 
-template <typename RT>
-static cudaError_t layered_t(const SolveArgs &a, int nt, RT *V, int16_t *policy, cudaStream_t st) {
+template <typename RT, int NO>
+static cudaError_t layered_t(const SolveArgs &a, int nt, const SolveIO &io, cudaStream_t st) {
   PipeRange pr0;
   size_t smem = 0;
   int blocks = 1;
   // every layer has the same number of slices (up to one straddling slice)
-  cudaError_t e = pipe_config<RT>(a, (a.Nc + a.spw - 1) / a.spw + 1, &pr0, &smem, &blocks);
+  cudaError_t e = pipe_config<RT, NO>(a, (a.Nc + a.spw - 1) / a.spw + 1, &pr0, &smem, &blocks);
   if (e != cudaSuccess) return e;
+  VSet<RT, NO> v;   // in place: layer t reads layer t+1, finished by the previous launch
+  for (int o = 0; o < NO; ++o) {
+    v.R[o] = static_cast<const RT *>(io.R[o]);
+    v.out[o] = static_cast<RT *>(io.V[o]);
+    v.in[o] = v.out[o];
+    v.pol[o] = io.policy[o];
+    v.res[o] = nullptr;
+  }
   for (int t = nt - 1; t >= 0; --t) {
     PipeRange pr = pr0;
     pr.s_lo = (int64_t)t * a.Nc;
     pr.s_hi = pr.s_lo + a.Nc;
     pr.sl_lo = pr.s_lo / a.spw;
     pr.sl_hi = (pr.s_hi + a.spw - 1) / a.spw;
-    bellman_kernel<RT><<<blocks, 32 * kWarps, smem, st>>>(a, V, V, policy, nullptr, 0, pr);
+    bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, 0, pr);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_layered(const SolveArgs &a, int precision, int nt, void *V, int16_t *policy,
-                           double *stats_d, cudaStream_t st) {
-  (void)stats_d;
-  if (precision == MDP_FP64_CHECK) return layered_t<double>(a, nt, (double *)V, policy, st);
-  return layered_t<float>(a, nt, (float *)V, policy, st);
+template <typename RT>
+static cudaError_t layered_n(const SolveArgs &a, int nt, const SolveIO &io, cudaStream_t st) {
+  switch (io.n) {
+    case 1: return layered_t<RT, 1>(a, nt, io, st);
+    case 2: return layered_t<RT, 2>(a, nt, io, st);
+    case 3: return layered_t<RT, 3>(a, nt, io, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, const SolveIO &io,
+                                 cudaStream_t st) {
+  if (precision == MDP_FP64_CHECK) return layered_n<double>(a, nt, io, st);
+  return layered_n<float>(a, nt, io, st);
 }
 
 // -------------------------------------------------------------- export ----

@@ -198,10 +198,21 @@ cudaError_t launch_build_warp_batch(const BuildArgs *items_d, const int64_t *pre
 cudaError_t launch_build_fp32_batch(const BuildArgs *items_d, int n, size_t smem, int threads,
                                     cudaStream_t st);
 size_t fp32_smem_bytes(const BuildArgs &a, int threads);
+// per-objective arrays of one solve over n <= 3 objectives sharing P
+struct SolveIO {
+  int n;
+  const void *R[3];           // objective slot bases of R
+  void *V[3], *Vtmp[3];       // V (the caller's output) and its Jacobi partner
+  int16_t *policy[3];
+};
+// stats_d: objective o's block at stats_d + o*(4 + max_sweeps); the error
+// word (a.err) is set by the caller
+cudaError_t launch_jacobi_multi(const SolveArgs &a, int precision, int max_sweeps, const SolveIO &io,
+                                double *stats_d, cudaStream_t st);
+cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, const SolveIO &io,
+                                 cudaStream_t st);
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st);
-cudaError_t launch_layered(const SolveArgs &a, int precision, int nt, void *V, int16_t *policy,
-                           double *stats_d, cudaStream_t st);
 // export
 cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_t *col,
                           int32_t *count, void *R, cudaStream_t st);

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mdp_export_csr": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
     "mdp_solve": (C.c_int, [P, C.c_int32, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_model_free": (None, [P]),
+    "mdp_solve_multi": (C.c_int, [P, C.c_int32, P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_solve_noalloc": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
                                     C.c_int32, P, P]),
@@ -266,6 +267,29 @@ def mdp_solve(model: Model, obj: int = 0, method: int = MDP_SOLVE_JACOBI, tol: f
     _check(load().mdp_solve(model.handle, obj, method, float(tol), int(max_sweeps), _ptr(V),
                             _ptr(policy), _stream(stream), C.byref(st)), "mdp_solve")
     return V, policy, st
+
+
+def mdp_solve_multi(model: Model, objs=(0,), method: int = MDP_SOLVE_JACOBI, tol: float = 0.0,
+                    max_sweeps: int = 0, V=None, policy=None, stream=None):
+    """Solves 1..3 objective slots in one fused pass over P per sweep.
+    Returns (list of V, list of policy, list of MdpSolveStats), one per slot."""
+    import torch
+    info = mdp_model_info(model)
+    n = len(objs)
+    dt = torch.float64 if model.precision else torch.float32
+    if V is None:
+        V = [torch.empty(info.n_states + 1, dtype=dt, device="cuda") for _ in range(n)]
+    if policy is None:
+        policy = [torch.empty(info.n_states, dtype=torch.int16, device="cuda") for _ in range(n)]
+    if len(V) != n or len(policy) != n:
+        raise ValueError("V and policy need one tensor per objective")
+    o_arr = (C.c_int32 * max(n, 1))(*objs)
+    v_arr = (C.c_void_p * max(n, 1))(*[_ptr(x) for x in V])
+    p_arr = (C.c_void_p * max(n, 1))(*[_ptr(x) for x in policy])
+    st = (MdpSolveStats * max(n, 1))()
+    _check(load().mdp_solve_multi(model.handle, n, o_arr, method, float(tol), int(max_sweeps), v_arr,
+                                  p_arr, _stream(stream), st), "mdp_solve_multi")
+    return list(V), list(policy), [st[i] for i in range(n)]
 
 
 def mdp_solve_noalloc(model: Model, obj: int = 0, tol: float = 0.0, max_sweeps: int = 0, V=None,
