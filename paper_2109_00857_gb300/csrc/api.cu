@@ -554,31 +554,33 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   }
   if (m->nS + m->Nc >= ((int64_t)1 << 31)) return arg_fail("more than 2^31 states is not supported by the solver");
   const bool jac = method == MDP_SOLVE_JACOBI;
-  // Jacobi partners: the model's cached buffer for the first objective,
-  // stream-ordered scratch for the others
-  if (jac && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
-  void *extra = nullptr;
-  if (jac && n > 1) MDP_CUDA_TRY(dev_alloc(&extra, vbytes * (size_t)(n - 1), st));
+  // n = 1 iterates in V and the model's cached partner buffer; n > 1 in
+  // packed value tables (stream-ordered scratch) copied out to V[o] at the end
+  if (n == 1 && jac && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
+  const size_t tbytes = fsz * (size_t)(n == 3 ? 4 : n) * (size_t)(m->nS + 1);
+  const int n_tables = n == 1 ? 0 : (jac ? 2 : 1);
+  void *tables = nullptr;
+  if (n_tables) MDP_CUDA_TRY(dev_alloc(&tables, tbytes * n_tables, st));
   const size_t blk = 4 + (size_t)max_sweeps;
   double *sd = nullptr;
   cudaError_t ce = dev_alloc((void **)&sd, sizeof(double) * blk * (size_t)n, st);
   if (ce != cudaSuccess) {
-    if (extra) dev_free(extra, st);
+    if (tables) dev_free(tables, st);
     return cuda_fail(ce, "dev_alloc");
   }
-  SolveIO io;
+  SolveIO io{};
   io.n = n;
   for (int o = 0; o < n; ++o) {
     io.R[o] = static_cast<const char *>(m->R) + fsz * (size_t)objs[o] * m->rows_pad;
     io.V[o] = V[o];
-    io.Vtmp[o] = !jac ? nullptr : (o == 0 ? m->Vtmp : static_cast<char *>(extra) + vbytes * (size_t)(o - 1));
     io.policy[o] = policy[o];
   }
-  for (int o = 0; o < n && ce == cudaSuccess; ++o) {
-    ce = cudaMemsetAsync(sd + o * blk, 0, sizeof(double) * 4, st);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(io.V[o], 0, vbytes, st);
-    if (ce == cudaSuccess && jac) ce = cudaMemsetAsync(io.Vtmp[o], 0, vbytes, st);
-  }
+  io.Vtmp[0] = (n == 1 && jac) ? m->Vtmp : nullptr;
+  for (int t = 0; t < n_tables; ++t) io.table[t] = static_cast<char *>(tables) + tbytes * t;
+  for (int o = 0; o < n && ce == cudaSuccess; ++o) ce = cudaMemsetAsync(sd + o * blk, 0, sizeof(double) * 4, st);
+  if (ce == cudaSuccess && n == 1) ce = cudaMemsetAsync(V[0], 0, vbytes, st);
+  if (ce == cudaSuccess && io.Vtmp[0]) ce = cudaMemsetAsync(io.Vtmp[0], 0, vbytes, st);
+  if (ce == cudaSuccess && tables) ce = cudaMemsetAsync(tables, 0, tbytes * n_tables, st);
   SolveArgs a;
   a.pool = m->pool; a.slice_off = m->slice_off; a.slice_w = m->slice_w; a.nnz = m->nnz;
   a.wcap = std::max(1, m->max_row_nnz);
@@ -593,14 +595,14 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   cudaEventRecord(e0, st);
   if (ce == cudaSuccess) {
     if (jac) ce = launch_jacobi_multi(a, m->precision, max_sweeps, io, sd, st);
-    else ce = launch_layered_multi(a, m->precision, m->nt, io, st);
+    else ce = launch_layered_multi(a, m->precision, m->nt, io, sd, st);
   }
   cudaEventRecord(e1, st);
   double hs[3][3] = {};
   for (int o = 0; o < n && ce == cudaSuccess; ++o)
     ce = cudaMemcpyAsync(hs[o], sd + o * blk, sizeof(hs[o]), cudaMemcpyDeviceToHost, st);
   dev_free(sd, st);
-  if (extra) dev_free(extra, st);
+  if (tables) dev_free(tables, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   float ms = 0.f;
   if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);

@@ -152,15 +152,26 @@ static int stage_bytes_for(int wcap, size_t rsz) {
 // res != nullptr: Jacobi sweep k (exits at once if sweep k-1 met the
 // tolerance) with the residual reduced into res[k-1].
 // One CTA, slices [b_lo, b_hi) of one model (all threads call it).
+// Values of NO objectives of one state, stored side by side (objective o
+// in v[o]; NO = 3 is padded to four) so that one vector load gathers V(s')
+// of every objective of a fused solve.
+template <typename RT, int NO>
+struct alignas(sizeof(RT) * (NO == 3 ? 4 : NO)) VPack {
+  static constexpr int W = (NO == 3) ? 4 : NO;
+  RT v[W];
+};
+
 // Per-objective operands of one Bellman launch.  NO objectives share the
 // streamed transition slices (each slice is copied once per sweep), each
-// with its own R, value buffers, policy and residual slots; res[o] ==
-// nullptr marks a layered pass (no residual, no early exit).
+// with its own R, policy and residual slots; their values live in one
+// packed table (in = V_k, out = V_{k+1}; equal for the in-place layered
+// pass).  res[o] == nullptr marks a layered pass (no residual, no early
+// exit).
 template <typename RT, int NO>
 struct VSet {
   const RT *R[NO];
-  const RT *in[NO];
-  RT *out[NO];
+  const VPack<RT, NO> *in;
+  VPack<RT, NO> *out;
   int16_t *pol[NO];
   unsigned long long *res[NO];
 };
@@ -258,15 +269,13 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
     // successor layer base of this state; rows without successors (last
     // layer, padding lanes) hold only padding words and read V[|S|] = 0
     const int sn = (s + Nc <= nS) ? s + Nc : nS;
-    const RT *Vn[NO];
-#pragma unroll
-    for (int o = 0; o < NO; ++o) Vn[o] = v.in[o] + sn;
+    const VPack<RT, NO> *Vn = v.in + sn;
 #pragma unroll 4
     for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
       const uint32_t w = ent[kk * 32];
-      const int off = (int)(int16_t)(w & 0xFFFFu);
+      const VPack<RT, NO> g = Vn[(int)(int16_t)(w & 0xFFFFu)];
 #pragma unroll
-      for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, Vn[o][off], a.N);
+      for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, g.v[o], a.N);
     }
     __syncwarp();
     if (j + kDepth < n_mine) issue(j + kDepth, st);   // refill the stage just read
@@ -276,6 +285,8 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
     }
     const bool head = act == 0 && s >= s_lo && s < s_hi;   // the lane that writes state s
     const bool term = head && __ldg(a.cls + s) != CLS_FREE;
+    VPack<RT, NO> old{}, nv;
+    if (head) old = v.in[s];
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
       RT qv = valid ? acc[o].q(Rv[o], invN) : -(RT)INFINITY;
@@ -298,14 +309,18 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
           }
         }
       }
-      if (head && ((live >> o) & 1u)) {
-        const RT old = v.in[o][s];
-        v.out[o][s] = qv;
+      // a finished objective carries its value forward unchanged
+      const bool upd = (live >> o) & 1u;
+      nv.v[o] = upd ? qv : old.v[o];
+      if (head && upd) {
         v.pol[o][s] = term ? (int16_t)-1 : (int16_t)qa;
-        if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv - old));
-        else r[o] = fmax(r[o], fabs(qv - old));
+        if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv - old.v[o]));
+        else r[o] = fmax(r[o], fabs(qv - old.v[o]));
       }
     }
+#pragma unroll
+    for (int o = NO; o < VPack<RT, NO>::W; ++o) nv.v[o] = (RT)0;
+    if (head) v.out[s] = nv;
   }
   if (v.res[0]) {
 #pragma unroll
@@ -315,10 +330,13 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
       if (lane == 0) wmax[warp * NO + o] = ro;
     }
     __syncthreads();
-    if (tid < NO) {
-      double m = 0.0;
-      for (int i = 0; i < kWarps; ++i) m = fmax(m, wmax[i * NO + tid]);
-      if (m > 0.0) atomicMax(&v.res[tid][k - 1], (unsigned long long)__double_as_longlong(m));
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {   // thread o publishes objective o (no dynamic index into v)
+      if (tid == o) {
+        double m = 0.0;
+        for (int i = 0; i < kWarps; ++i) m = fmax(m, wmax[i * NO + o]);
+        if (m > 0.0) atomicMax(&v.res[o][k - 1], (unsigned long long)__double_as_longlong(m));
+      }
     }
   }
 }
@@ -356,8 +374,8 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   pr.dtab_smem = 0;
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
-  v.in[0] = (k & 1) ? it.Va : it.Vb;
-  v.out[0] = (k & 1) ? it.Vb : it.Va;
+  v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
+  v.out = reinterpret_cast<VPack<float, 1> *>((k & 1) ? it.Vb : it.Va);
   v.pol[0] = it.policy;
   v.res[0] = it.res;
   bellman_body<float, 1>(it.a, v, k, c.sl_lo, c.sl_hi, pr, sm, wmax, wst_s);
@@ -443,24 +461,67 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
   return cudaSuccess;
 }
 
+// Fused solve epilogue: objective o's sweep count is the first k whose
+// residual met tol (else max_sweeps); the table of the last executed sweep
+// (the largest count; 0 = the initial table) holds every objective's final
+// values, since a finished objective is carried forward unchanged.  Writes
+// the stats and copies objective o's column into V[o][0..n).
+template <typename RT, int NO>
+struct VOut {
+  RT *V[NO];
+};
+template <typename RT, int NO>
+__global__ void finalize_multi_kernel(const double *stats_base, size_t blk, int max_sweeps, double tol,
+                                      const VPack<RT, NO> *ta, const VPack<RT, NO> *tb, VOut<RT, NO> out,
+                                      int64_t n, double *stats_out, int layered) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    int last = 0;
+    for (int o = 0; o < NO; ++o) {
+      const unsigned long long *res = reinterpret_cast<const unsigned long long *>(stats_base + o * blk + 4);
+      int sw = max_sweeps;
+      if (!layered) {
+        for (int k = 1; k <= max_sweeps; ++k)
+          if (__longlong_as_double((long long)res[k - 1]) <= tol) { sw = k; break; }
+      }
+      last = max(last, sw);
+      if (blockIdx.x == 0 && !layered) {
+        stats_out[o * blk + 0] = (double)sw;
+        stats_out[o * blk + 1] = sw > 0 ? __longlong_as_double((long long)res[sw - 1]) : 0.0;
+      }
+    }
+    s_last = layered ? 0 : last;
+  }
+  __syncthreads();
+  const VPack<RT, NO> *t = (s_last & 1) ? tb : ta;   // sweep k writes tb when k is odd
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const VPack<RT, NO> p = t[i];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) out.V[o][i] = p.v[o];
+  }
+}
+
 // Objective o's status block: stats_d + o*(4 + max_sweeps) holds sweeps,
 // residual, (objective 0: the error word), spare, then one residual slot
-// per sweep.
+// per sweep.  NO = 1 iterates in the caller's V and io.Vtmp[0]; NO > 1 in
+// the packed tables io.table[0..1], copied out to V[o] at the end.
 template <typename RT, int NO>
 static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, const SolveIO &io, double *stats_d,
                             cudaStream_t st) {
+  using Pk = VPack<RT, NO>;
   const size_t blk = 4 + (size_t)max_sweeps;
-  VSet<RT, NO> odd, even;   // sweep k reads Va when k is odd, Vb when even
+  Pk *ta = static_cast<Pk *>(NO == 1 ? io.V[0] : io.table[0]);
+  Pk *tb = static_cast<Pk *>(NO == 1 ? io.Vtmp[0] : io.table[1]);
+  VSet<RT, NO> odd, even;   // sweep k reads ta when k is odd, tb when even
+  odd.in = ta;
+  odd.out = tb;
+  even.in = tb;
+  even.out = ta;
   for (int o = 0; o < NO; ++o) {
     unsigned long long *res = reinterpret_cast<unsigned long long *>(stats_d + o * blk + 4);
     cudaError_t e = cudaMemsetAsync(res, 0, sizeof(unsigned long long) * (size_t)max_sweeps, st);
     if (e != cudaSuccess) return e;
     odd.R[o] = even.R[o] = static_cast<const RT *>(io.R[o]);
-    RT *va = static_cast<RT *>(io.V[o]), *vb = static_cast<RT *>(io.Vtmp[o]);
-    odd.in[o] = va;
-    odd.out[o] = vb;
-    even.in[o] = vb;
-    even.out[o] = va;
     odd.pol[o] = even.pol[o] = io.policy[o];
     odd.res[o] = even.res[o] = res;
   }
@@ -479,10 +540,14 @@ static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, const SolveIO &i
   if (e != cudaSuccess) return e;
   int64_t fb = (a.nS + 1 + 255) / 256;
   if (fb > 1024) fb = 1024;
-  for (int o = 0; o < NO; ++o) {
-    finalize_kernel<RT><<<(unsigned)fb, 256, 0, st>>>(odd.res[o], max_sweeps, a.tol, static_cast<RT *>(io.V[o]),
-                                                       static_cast<const RT *>(io.Vtmp[o]), a.nS + 1,
-                                                       stats_d + o * blk);
+  if constexpr (NO == 1) {
+    finalize_kernel<RT><<<(unsigned)fb, 256, 0, st>>>(odd.res[0], max_sweeps, a.tol, static_cast<RT *>(io.V[0]),
+                                                       static_cast<const RT *>(io.Vtmp[0]), a.nS + 1, stats_d);
+  } else {
+    VOut<RT, NO> out;
+    for (int o = 0; o < NO; ++o) out.V[o] = static_cast<RT *>(io.V[o]);
+    finalize_multi_kernel<RT, NO><<<(unsigned)fb, 256, 0, st>>>(stats_d, blk, max_sweeps, a.tol, ta, tb, out,
+                                                                 a.nS + 1, stats_d, 0);
   }
   return cudaGetLastError();
 }
@@ -506,7 +571,7 @@ cudaError_t launch_jacobi_multi(const SolveArgs &a, int precision, int max_sweep
 
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st) {
-  SolveIO io;
+  SolveIO io{};
   io.n = 1;
   io.R[0] = a.R;
   io.V[0] = Va;
@@ -515,47 +580,60 @@ cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, voi
   return launch_jacobi_multi(a, precision, max_sweeps, io, stats_d, st);
 }
 
+// In place: layer t reads layer t+1, finished by the previous launch.
 template <typename RT, int NO>
-static cudaError_t layered_t(const SolveArgs &a, int nt, const SolveIO &io, cudaStream_t st) {
+static cudaError_t layered_t(const SolveArgs &a, int nt, const SolveIO &io, double *stats_d,
+                             cudaStream_t st) {
+  using Pk = VPack<RT, NO>;
   PipeRange pr0;
   size_t smem = 0;
   int blocks = 1;
   // every layer has the same number of slices (up to one straddling slice)
   cudaError_t e = pipe_config<RT, NO>(a, (a.Nc + a.spw - 1) / a.spw + 1, &pr0, &smem, &blocks);
   if (e != cudaSuccess) return e;
-  VSet<RT, NO> v;   // in place: layer t reads layer t+1, finished by the previous launch
+  VSet<RT, NO> v;
+  Pk *t = static_cast<Pk *>(NO == 1 ? io.V[0] : io.table[0]);
+  v.in = t;
+  v.out = t;
   for (int o = 0; o < NO; ++o) {
     v.R[o] = static_cast<const RT *>(io.R[o]);
-    v.out[o] = static_cast<RT *>(io.V[o]);
-    v.in[o] = v.out[o];
     v.pol[o] = io.policy[o];
     v.res[o] = nullptr;
   }
-  for (int t = nt - 1; t >= 0; --t) {
+  for (int t_ = nt - 1; t_ >= 0; --t_) {
     PipeRange pr = pr0;
-    pr.s_lo = (int64_t)t * a.Nc;
+    pr.s_lo = (int64_t)t_ * a.Nc;
     pr.s_hi = pr.s_lo + a.Nc;
     pr.sl_lo = pr.s_lo / a.spw;
     pr.sl_hi = (pr.s_hi + a.spw - 1) / a.spw;
     bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, 0, pr);
   }
+  e = cudaGetLastError();
+  if (e != cudaSuccess || NO == 1) return e;
+  VOut<RT, NO> out;
+  for (int o = 0; o < NO; ++o) out.V[o] = static_cast<RT *>(io.V[o]);
+  int64_t fb = (a.nS + 1 + 255) / 256;
+  if (fb > 1024) fb = 1024;
+  finalize_multi_kernel<RT, NO><<<(unsigned)fb, 256, 0, st>>>(stats_d, 0, 0, a.tol, t, t, out, a.nS + 1,
+                                                               stats_d, 1);
   return cudaGetLastError();
 }
 
 template <typename RT>
-static cudaError_t layered_n(const SolveArgs &a, int nt, const SolveIO &io, cudaStream_t st) {
+static cudaError_t layered_n(const SolveArgs &a, int nt, const SolveIO &io, double *stats_d,
+                             cudaStream_t st) {
   switch (io.n) {
-    case 1: return layered_t<RT, 1>(a, nt, io, st);
-    case 2: return layered_t<RT, 2>(a, nt, io, st);
-    case 3: return layered_t<RT, 3>(a, nt, io, st);
+    case 1: return layered_t<RT, 1>(a, nt, io, stats_d, st);
+    case 2: return layered_t<RT, 2>(a, nt, io, stats_d, st);
+    case 3: return layered_t<RT, 3>(a, nt, io, stats_d, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, const SolveIO &io,
-                                 cudaStream_t st) {
-  if (precision == MDP_FP64_CHECK) return layered_n<double>(a, nt, io, st);
-  return layered_n<float>(a, nt, io, st);
+                                 double *stats_d, cudaStream_t st) {
+  if (precision == MDP_FP64_CHECK) return layered_n<double>(a, nt, io, stats_d, st);
+  return layered_n<float>(a, nt, io, stats_d, st);
 }
 
 // -------------------------------------------------------------- export ----

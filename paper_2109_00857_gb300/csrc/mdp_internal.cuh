@@ -202,7 +202,10 @@ size_t fp32_smem_bytes(const BuildArgs &a, int threads);
 struct SolveIO {
   int n;
   const void *R[3];           // objective slot bases of R
-  void *V[3], *Vtmp[3];       // V (the caller's output) and its Jacobi partner
+  void *V[3];                 // the caller's outputs
+  void *Vtmp[3];              // n = 1: the Jacobi partner of V[0]
+  void *table[2];             // n > 1: packed value tables [|S|+1][n == 3 ? 4 : n]
+                              // (Jacobi: both, layered: table[0]), zeroed by the caller
   int16_t *policy[3];
 };
 // stats_d: objective o's block at stats_d + o*(4 + max_sweeps); the error
@@ -210,7 +213,7 @@ struct SolveIO {
 cudaError_t launch_jacobi_multi(const SolveArgs &a, int precision, int max_sweeps, const SolveIO &io,
                                 double *stats_d, cudaStream_t st);
 cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, const SolveIO &io,
-                                 cudaStream_t st);
+                                 double *stats_d, cudaStream_t st);
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st);
 // export
