@@ -167,15 +167,21 @@ mdp_status mdp_export_csr(mdp_model m, int32_t obj, int64_t *rowptr, int64_t *co
 
 /* Solve schedules. */
 typedef enum {
-  MDP_SOLVE_JACOBI = 0,    /* Gauss-Jacobi sweeps over all states, device residual (Sec. II-B) */
-  MDP_SOLVE_LAYERED = 1    /* one backward pass over time layers t = nt-1..0 (same fixed point) */
+  MDP_SOLVE_JACOBI = 0,       /* Jacobi sweeps V_{k+1} = T V_k with a device residual (Sec. II-B).
+                                * A sweep recomputes only the time layers t whose own values or
+                                * whose successor layer t+1 changed in the previous sweep; every
+                                * other state has V_{k+1}(s) = V_k(s) exactly, so iterates, policy,
+                                * residuals and sweep count equal MDP_SOLVE_JACOBI_FULL bit for bit */
+  MDP_SOLVE_LAYERED = 1,      /* one backward pass over time layers t = nt-1..0 (same fixed point) */
+  MDP_SOLVE_JACOBI_FULL = 2   /* Jacobi sweeps over every state in every sweep */
 } mdp_solve_method;
 
 typedef struct {
   int32_t sweeps;          /* sweeps executed (layered: 1) */
   double residual;         /* max |V_k - V_{k-1}| of the last sweep (layered: 0) */
   double solve_ms;         /* device time of the solve kernels (CUDA events) */
-  int64_t backups;         /* (s,a) Bellman backups performed */
+  int64_t backups;         /* (s,a) Bellman backups computed (MDP_SOLVE_JACOBI: the
+                            * recomputed layers only; fused solves: for all objectives) */
 } mdp_solve_stats;
 
 /* Value iteration on the model's P and the R of objective slot obj.
@@ -209,8 +215,10 @@ mdp_status mdp_solve_multi(mdp_model m, int32_t n, const int32_t *objs, int32_t 
  * a real-time replanning loop that must not block or fragment its memory
  * budget, or a program whose device memory belongs to another allocator.
  * The paper has no counterpart of this call.  Its scratch (the second value
- * buffer, the residual slots and status words) is a fixed array inside the
- * library, 8 MiB + 32 KiB per GPU, held by every GPU that loads the library
+ * buffer, the residual slots, status words, per-sweep work counts and the
+ * layer flags of the active-layer sweeps; models with more than 4095 time
+ * layers run full sweeps, same results) is a fixed array inside the
+ * library, 8 MiB + 76 KiB per GPU, held by every GPU that loads the library
  * until the process exits; it performs no cudaMalloc or cudaFree.
  * Limits: (|S| + 1) values must fit 8 MiB (at most 2,097,151 states in FP32,
  * 1,048,575 in FP64_CHECK) and max_sweeps (0 = nt + 1) must be <= 4092;

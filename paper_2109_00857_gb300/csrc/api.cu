@@ -539,7 +539,8 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
     if (!V[o] || !policy[o]) return arg_fail("NULL V or policy");
     if (objs[o] < 0 || objs[o] >= m->n_obj) return arg_fail("objective slot out of range");
   }
-  if (method != MDP_SOLVE_JACOBI && method != MDP_SOLVE_LAYERED) return arg_fail("method");
+  if (method != MDP_SOLVE_JACOBI && method != MDP_SOLVE_LAYERED && method != MDP_SOLVE_JACOBI_FULL)
+    return arg_fail("method");
   if (!(tol >= 0) && !(tol < 0)) return arg_fail("tol is NaN");
   if (max_sweeps < 0) return arg_fail("max_sweeps must be >= 0");
   if (max_sweeps == 0) max_sweeps = m->nt + 1;
@@ -553,7 +554,8 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
     return MDP_ERR_CUDA;
   }
   if (m->nS + m->Nc >= ((int64_t)1 << 31)) return arg_fail("more than 2^31 states is not supported by the solver");
-  const bool jac = method == MDP_SOLVE_JACOBI;
+  const bool jac = method != MDP_SOLVE_LAYERED;
+  const bool active = method == MDP_SOLVE_JACOBI;   // active-layer sweeps
   // n = 1 iterates in V and the model's cached partner buffer; n > 1 in
   // packed value tables (stream-ordered scratch) copied out to V[o] at the end
   if (n == 1 && jac && !m->Vtmp) MDP_CUDA_TRY(dev_alloc(&m->Vtmp, vbytes, st));
@@ -561,9 +563,12 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   const int n_tables = n == 1 ? 0 : (jac ? 2 : 1);
   void *tables = nullptr;
   if (n_tables) MDP_CUDA_TRY(dev_alloc(&tables, tbytes * n_tables, st));
+  // status blocks, then (active-layer Jacobi) the per-sweep work counts and
+  // the three rotating layer-flag arrays
   const size_t blk = 4 + (size_t)max_sweeps;
+  const size_t n_dbl = blk * (size_t)n + (active ? (size_t)max_sweeps + (3 * ((size_t)m->nt + 1) + 7) / 8 : 0);
   double *sd = nullptr;
-  cudaError_t ce = dev_alloc((void **)&sd, sizeof(double) * blk * (size_t)n, st);
+  cudaError_t ce = dev_alloc((void **)&sd, sizeof(double) * n_dbl, st);
   if (ce != cudaSuccess) {
     if (tables) dev_free(tables, st);
     return cuda_fail(ce, "dev_alloc");
@@ -589,6 +594,11 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;
   a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
   a.err = reinterpret_cast<int *>(sd + 2);
+  a.nt = m->nt;
+  if (active) {
+    a.work = reinterpret_cast<unsigned long long *>(sd + blk * n);
+    a.lflags = reinterpret_cast<uint8_t *>(sd + blk * n + max_sweeps);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -601,6 +611,9 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   double hs[3][3] = {};
   for (int o = 0; o < n && ce == cudaSuccess; ++o)
     ce = cudaMemcpyAsync(hs[o], sd + o * blk, sizeof(hs[o]), cudaMemcpyDeviceToHost, st);
+  std::vector<unsigned long long> work(active ? max_sweeps : 0);
+  if (active && ce == cudaSuccess)
+    ce = cudaMemcpyAsync(work.data(), a.work, sizeof(unsigned long long) * max_sweeps, cudaMemcpyDeviceToHost, st);
   dev_free(sd, st);
   if (tables) dev_free(tables, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -620,7 +633,13 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
       stats[o].sweeps = jac ? (int32_t)hs[o][0] : 1;
       stats[o].residual = jac ? hs[o][1] : 0.0;
       stats[o].solve_ms = ms;
-      stats[o].backups = (int64_t)stats[o].sweeps * m->nS * m->A;
+      if (active) {   // slices recomputed in the objective's sweeps
+        int64_t sl = 0;
+        for (int k = 0; k < stats[o].sweeps; ++k) sl += (int64_t)work[k];
+        stats[o].backups = std::min<int64_t>(sl * m->spw, (int64_t)stats[o].sweeps * m->nS) * m->A;
+      } else {
+        stats[o].backups = (int64_t)stats[o].sweeps * m->nS * m->A;
+      }
     }
   }
   return MDP_OK;

@@ -189,6 +189,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   }
   if (!live) return;
   if (*(volatile int *)a.err) return;   // an earlier launch of this solve timed out
+  if (a.work && k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) a.work[k - 1] = (unsigned long long)(pr.sl_hi - pr.sl_lo);
   uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // [kWarps][kDepth]
   unsigned char *ring = sm + 256;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -250,6 +251,11 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   uint32_t phase = 0;
   int s = sl0 * a.spw + q;                      // state of this lane's row in my j-th slice
   const int s_step = kWarps * a.spw;
+  // active-layer Jacobi: layer t_cur of my state s (s < t_end = (t_cur+1) Nc)
+  // and whether any of its values changed in this sweep
+  uint8_t *chg_out = a.lflags ? a.lflags + (size_t)(k % 3) * (a.nt + 1) : nullptr;
+  int t_cur = s / Nc, t_end = (t_cur + 1) * Nc;
+  bool chg = false;
   for (int j = 0; j < n_mine; ++j, s += s_step) {
     if (!mbar_wait(bar0 + 8u * (uint32_t)st, phase)) {
       if (lane == 0) atomicOr(a.err, 1);
@@ -320,8 +326,23 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
     }
 #pragma unroll
     for (int o = NO; o < VPack<RT, NO>::W; ++o) nv.v[o] = (RT)0;
-    if (head) v.out[s] = nv;
+    if (head) {
+      v.out[s] = nv;
+      if (chg_out) {
+        if (s >= t_end) {   // entered a later layer: publish the finished one
+          if (chg) chg_out[t_cur] = 1;
+          chg = false;
+          do { ++t_cur; t_end += Nc; } while (s >= t_end);
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {   // bitwise: -0 vs +0 counts as a change
+          if constexpr (sizeof(RT) == 4) chg |= __float_as_uint(nv.v[o]) != __float_as_uint(old.v[o]);
+          else chg |= __double_as_longlong(nv.v[o]) != __double_as_longlong(old.v[o]);
+        }
+      }
+    }
   }
+  if (chg_out && chg) chg_out[t_cur] = 1;
   if (v.res[0]) {
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
@@ -341,12 +362,47 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   }
 }
 
+// Active-layer Jacobi sweep k: layer t needs recomputing if its own values
+// or those of layer t+1 changed in sweep k-1 (otherwise V_{k+1} = V_k on it
+// and the output table already holds that value from sweep k-1).  Narrows
+// [sl_lo, sl_hi) to the slices of the first through the last such layer
+// (layers in between are recomputed, which yields their unchanged values).
+// CTA 0 clears the flags that sweep k+1 will set.  Returns false when no
+// layer changed: V_{k+1} = V_k, the residual stays 0.  All threads call it.
+__device__ __forceinline__ bool active_range(const SolveArgs &a, int k, PipeRange &pr) {
+  const int nt = a.nt;
+  const uint8_t *prev = a.lflags + (size_t)((k - 1) % 3) * (nt + 1);
+  if (blockIdx.x == 0) {
+    uint8_t *clr = a.lflags + (size_t)((k + 1) % 3) * (nt + 1);
+    for (int t = threadIdx.x; t <= nt; t += blockDim.x) clr[t] = 0;
+  }
+  __shared__ int s_tlo, s_thi;
+  if (threadIdx.x == 0) {
+    s_tlo = nt;
+    s_thi = -1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    if (prev[t] | prev[t + 1]) {
+      atomicMin(&s_tlo, t);
+      atomicMax(&s_thi, t);
+    }
+  }
+  __syncthreads();
+  const int tlo = s_tlo, thi = s_thi;
+  if (thi < 0) return false;
+  pr.sl_lo = (int64_t)tlo * a.Nc / a.spw;
+  pr.sl_hi = min(a.n_slices, ((int64_t)(thi + 1) * a.Nc + a.spw - 1) / a.spw);
+  return true;
+}
+
 template <typename RT, int NO>
 __global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, VSet<RT, NO> v, int k,
                                                               PipeRange pr) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double wmax[kWarps * NO];
   __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
+  if (a.lflags && k >= 1 && !active_range(a, k, pr)) return;
   const int64_t total = pr.sl_hi - pr.sl_lo;
   const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
   const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
@@ -524,6 +580,12 @@ static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, const SolveIO &i
     odd.R[o] = even.R[o] = static_cast<const RT *>(io.R[o]);
     odd.pol[o] = even.pol[o] = io.policy[o];
     odd.res[o] = even.res[o] = res;
+  }
+  if (a.lflags) {   // sweep 1 recomputes every layer
+    cudaError_t e = cudaMemsetAsync(a.lflags, 1, (size_t)a.nt, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.lflags + a.nt, 0, (size_t)a.nt + 2, st);
+    if (e == cudaSuccess && a.work) e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long) * max_sweeps, st);
+    if (e != cudaSuccess) return e;
   }
   PipeRange pr;
   size_t smem = 0;

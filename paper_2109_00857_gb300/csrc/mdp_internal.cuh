@@ -171,6 +171,13 @@ struct SolveArgs {
   int64_t nS, Nc, n_slices;
   int32_t A, A_pad, spw, N, nbins;
   double tol;
+  // Active-layer Jacobi (nullptr: every state every sweep).  lflags holds
+  // three rotating arrays of nt + 1 layer flags: sweep k reads
+  // lflags[(k-1)%3] (layers whose V changed in sweep k-1; entry nt, the
+  // sink, stays 0), sets lflags[k%3] and clears lflags[(k+1)%3].
+  uint8_t *lflags = nullptr;
+  unsigned long long *work = nullptr;   // [max_sweeps] slices computed per sweep (or nullptr)
+  int32_t nt = 0;
 };
 // batched solve (FP32): one Jacobi sweep over many models per launch
 struct BatchSolveItem {

@@ -8,6 +8,7 @@
 // application whose device memory is owned by another allocator that hands
 // out no extra space.  mdp_solve_noalloc() runs the same kernels with its
 // scratch in the fixed array below instead.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -16,10 +17,16 @@
 namespace mdpgb {
 
 // Scratch layout: [0, kVBytes) the partner value buffer; then 4 status
-// doubles (sweeps, residual, error word) and one residual slot per sweep.
+// doubles (sweeps, residual, error word) and one residual slot per sweep;
+// one work count per sweep; three arrays of kLayers layer flags for the
+// active-layer sweeps (models with more than kLayers - 1 time layers run
+// full sweeps, which give the same results).
 constexpr size_t kNoAllocVBytes = 8u << 20;                        // 8 MiB
 constexpr size_t kNoAllocSweeps = 4092;
-constexpr size_t kNoAllocBytes = kNoAllocVBytes + 8 * (4 + kNoAllocSweeps);   // 8 MiB + 32 KiB
+constexpr size_t kNoAllocLayers = 4096;
+constexpr size_t kNoAllocStatus = 8 * (4 + kNoAllocSweeps);
+constexpr size_t kNoAllocWork = 8 * kNoAllocSweeps;
+constexpr size_t kNoAllocBytes = kNoAllocVBytes + kNoAllocStatus + kNoAllocWork + 3 * kNoAllocLayers;   // 8 MiB + 76 KiB
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -111,9 +118,17 @@ extern "C" mdp_status mdp_solve_noalloc(mdp_model m, int32_t obj, double tol, in
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;
   a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
   a.err = reinterpret_cast<int *>(sd + 2);
+  a.nt = m->nt;
+  if ((size_t)m->nt + 1 <= kNoAllocLayers) {
+    a.work = reinterpret_cast<unsigned long long *>(scratch + kNoAllocVBytes + kNoAllocStatus);
+    a.lflags = scratch + kNoAllocVBytes + kNoAllocStatus + kNoAllocWork;
+  }
   MDP_CUDA_TRY(launch_jacobi(a, m->precision, max_sweeps, V, Vb, policy, sd, st));
   double hs[3] = {0, 0, 0};
+  unsigned long long wk[kNoAllocSweeps];   // per-sweep work counts (host stack, no allocation)
   MDP_CUDA_TRY(cudaMemcpyAsync(hs, sd, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  if (a.work)
+    MDP_CUDA_TRY(cudaMemcpyAsync(wk, a.work, sizeof(unsigned long long) * max_sweeps, cudaMemcpyDeviceToHost, st));
   MDP_CUDA_TRY(cudaStreamSynchronize(st));
   int errw = 0;
   memcpy(&errw, &hs[2], sizeof(int));
@@ -126,6 +141,11 @@ extern "C" mdp_status mdp_solve_noalloc(mdp_model m, int32_t obj, double tol, in
     stats->residual = hs[1];
     stats->solve_ms = 0.0;
     stats->backups = (int64_t)stats->sweeps * m->nS * m->A;
+    if (a.work) {   // slices recomputed by the active-layer sweeps
+      int64_t sl = 0;
+      for (int k = 0; k < stats->sweeps; ++k) sl += (int64_t)wk[k];
+      stats->backups = std::min<int64_t>(sl * m->spw, (int64_t)stats->sweeps * m->nS) * m->A;
+    }
   }
   return MDP_OK;
 }

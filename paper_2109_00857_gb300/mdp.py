@@ -23,7 +23,7 @@ STATUS = {0: "MDP_OK", -1: "MDP_ERR_ARG", -2: "MDP_ERR_OOM", -3: "MDP_ERR_SUBGRI
           -10: "MDP_ERR_PENDING"}
 MDP_OBJ_TIME, MDP_OBJ_ENERGY, MDP_OBJ_NET_ENERGY = 0, 1, 2
 MDP_FP32, MDP_FP64_CHECK = 0, 1
-MDP_SOLVE_JACOBI, MDP_SOLVE_LAYERED = 0, 1
+MDP_SOLVE_JACOBI, MDP_SOLVE_LAYERED, MDP_SOLVE_JACOBI_FULL = 0, 1, 2
 
 P = C.c_void_p
 

@@ -305,6 +305,46 @@ def test_layered_schedule_equals_jacobi_bitwise(mdp):
         assert np.array_equal(pij.cpu().numpy(), pil.cpu().numpy())
 
 
+ACTIVE_CASES = {
+    "three_objectives": lambda: inputs.large(nx=22, ny=22, nt=9, N=300, L=15, square=5),
+    "A12_straddling_slices": lambda: inputs.make_env(nx=9, ny=7, nt=8, K=3, N=250, L=9,
+                                                     sigma=(0.3, 0.2, 0.1), seed=5, amplitude=0.8,
+                                                     n_headings=12, n_speeds=1, obstacle="squares",
+                                                     square=3),
+    "tiny_rterm": lambda: inputs.tiny(nx=13, ny=11, nt=12, N=77, r_term=4.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(ACTIVE_CASES))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_active_layer_jacobi_equals_full_sweeps_bitwise(mdp, case, precision):
+    # the active-layer schedule recomputes only layers whose inputs changed;
+    # iterates, policy, sweep count and residual must equal full sweeps exactly
+    env = ACTIVE_CASES[case]()
+    prec = mdp.MDP_FP32 if precision == "fp32" else mdp.MDP_FP64_CHECK
+    model = mdp.mdp_build(mdp.DeviceEnv(env, prec), objs=env.objectives)
+    n = len(env.objectives)
+    for tol, ms in ((0.0, 0), (0.0, 3), (1e-3, 0), (0.5, 0)):
+        for o in range(n):
+            Va, pa, sa = mdp.mdp_solve(model, o, method=mdp.MDP_SOLVE_JACOBI, tol=tol, max_sweeps=ms)
+            Vf, pf, sf = mdp.mdp_solve(model, o, method=mdp.MDP_SOLVE_JACOBI_FULL, tol=tol, max_sweeps=ms)
+            assert np.array_equal(Va.cpu().numpy().view(np.uint8), Vf.cpu().numpy().view(np.uint8))
+            assert np.array_equal(pa.cpu().numpy(), pf.cpu().numpy())
+            assert (sa.sweeps, sa.residual) == (sf.sweeps, sf.residual)
+            assert sa.backups <= sf.backups
+            if tol == 0.0 and ms == 0:   # later sweeps skip the layers that are final
+                assert sa.backups < sf.backups
+        if n > 1:
+            objs = tuple(range(n))
+            Vs, ps, ss = mdp.mdp_solve_multi(model, objs, method=mdp.MDP_SOLVE_JACOBI, tol=tol, max_sweeps=ms)
+            Vg, pg, sg = mdp.mdp_solve_multi(model, objs, method=mdp.MDP_SOLVE_JACOBI_FULL, tol=tol,
+                                             max_sweeps=ms)
+            for o in range(n):
+                assert np.array_equal(Vs[o].cpu().numpy().view(np.uint8), Vg[o].cpu().numpy().view(np.uint8))
+                assert np.array_equal(ps[o].cpu().numpy(), pg[o].cpu().numpy())
+                assert (ss[o].sweeps, ss[o].residual) == (sg[o].sweeps, sg[o].residual)
+
+
 def test_solver_tolerance_stops_early_and_max_sweeps(mdp):
     env = inputs.tiny(nx=12, ny=12, nt=8, N=100, r_term=5.0)
     model = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP64_CHECK))
