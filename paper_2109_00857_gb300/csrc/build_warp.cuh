@@ -87,11 +87,18 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
   return make_float2(ux, uy);
 }
 
-__device__ __forceinline__ void count_sample(float ux, float uy, float dxl, float dyl,
-                                             uint32_t rowstride, uint32_t hb) {
-  const uint32_t bx = __float_as_uint(__fadd_rd(ux + dxl, kMagic));
-  const uint32_t by = __float_as_uint(__fadd_rd(uy + dyl, kMagic));
-  red_add_shared(by * rowstride + bx * 128u + hb, 1u);
+// Counts one landing: (x, y) = u + d_a rounded to nearest, then floor of both
+// by a round-down add of the magic constant, in packed f32x2 adds (two
+// lanes' worth of FP32 work per instruction, same IEEE results as scalar
+// adds); the floors' bit patterns index the lane's histogram column.
+// u, d: (x, y) pairs as 64-bit registers (x in the low word).
+constexpr unsigned long long kMagic2 = ((unsigned long long)kMagicBits << 32) | kMagicBits;
+__device__ __forceinline__ void count_sample(unsigned long long u, unsigned long long d, uint32_t rowstride,
+                                             uint32_t hb) {
+  unsigned long long p, f;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(u), "l"(d));
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(f) : "l"(p), "l"(kMagic2));
+  red_add_shared((uint32_t)(f >> 32) * rowstride + (uint32_t)f * 128u + hb, 1u);
 }
 
 // Per-warp totals, added to the model's counters by warp_flush().
@@ -216,7 +223,8 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     const uint32_t rowstride = (uint32_t)pitch * 128u;
     const uint32_t hb = hist_base - (kMagicBits + (uint32_t)loy) * rowstride -
                         (kMagicBits + (uint32_t)lox) * 128u;
-    const float4 *ub4 = reinterpret_cast<const float4 *>(ubuf + q_l * CHq);
+    const ulonglong2 *ub4 = reinterpret_cast<const ulonglong2 *>(ubuf + q_l * CHq);
+    const unsigned long long d2 = ((unsigned long long)__float_as_uint(dyl) << 32) | __float_as_uint(dxl);
     for (int c0 = 0; c0 < a.N; c0 += CHq) {
       if (kind_t == KIND_SAMPLE) {
 #pragma unroll
@@ -234,24 +242,21 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
           if constexpr (SPW > 0) {
 #pragma unroll
             for (int p = 0; p < kItems / SPW / 2; ++p) {
-              const float4 u2 = ub4[p];
-              count_sample(u2.x, u2.y, dxl, dyl, rowstride, hb);
-              count_sample(u2.z, u2.w, dxl, dyl, rowstride, hb);
+              const ulonglong2 u2 = ub4[p];
+              count_sample(u2.x, d2, rowstride, hb);
+              count_sample(u2.y, d2, rowstride, hb);
             }
           } else {
 #pragma unroll 4
             for (int p = 0; p < CHq / 2; ++p) {
-              const float4 u2 = ub4[p];
-              count_sample(u2.x, u2.y, dxl, dyl, rowstride, hb);
-              count_sample(u2.z, u2.w, dxl, dyl, rowstride, hb);
+              const ulonglong2 u2 = ub4[p];
+              count_sample(u2.x, d2, rowstride, hb);
+              count_sample(u2.y, d2, rowstride, hb);
             }
           }
         } else {
-          const float2 *ub = ubuf + q_l * CHq;
-          for (int wl = 0; wl < a.N - c0; ++wl) {
-            const float2 u = ub[wl];
-            count_sample(u.x, u.y, dxl, dyl, rowstride, hb);
-          }
+          const unsigned long long *ub = reinterpret_cast<const unsigned long long *>(ubuf + q_l * CHq);
+          for (int wl = 0; wl < a.N - c0; ++wl) count_sample(ub[wl], d2, rowstride, hb);
         }
       }
       __syncwarp();
