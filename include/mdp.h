@@ -114,8 +114,9 @@ typedef struct {
   int32_t no_compact;      /* 1: keep the worst-case entry pool instead of compacting it */
   int32_t threads;         /* build CTA size for FP32 (multiple of 64); 0 = autotuned */
   int32_t chunk;           /* realizations staged per pass; 0 = autotuned */
-  int32_t hist_cap;        /* per-row histogram bins of the warp-per-slice kernel; 0 = 64;
-                              slices wider than this go to the full-window kernel
+  int32_t hist_cap;        /* fine-count table cells (32-bit words) per warp of the
+                              warp-per-slice kernel, <= 6144; 0 = 2048; slices whose
+                              tables need more go to the full-window kernel
                               (1 sends every sampled slice there) */
 } mdp_build_opts;
 
@@ -151,7 +152,7 @@ typedef struct {
   double build_ms;         /* device time of sampler + build kernels (CUDA events) */
   double kernel_ms;        /* device time of the fused build kernel alone (CUDA events) */
   int32_t launches;        /* kernels the build launched */
-  int64_t wide_slices;     /* slices built by the full-window kernel (histogram > hist_cap) */
+  int64_t wide_slices;     /* slices built by the full-window kernel (tables > hist_cap) */
   int64_t nnz_domain;      /* stored successors inside the domain (sink entries excluded) */
 } mdp_model_info_t;
 

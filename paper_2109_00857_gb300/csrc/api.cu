@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/mdp.h: argument checks, device memory,
 // launch sequencing and status read-back for build, export, solve and the
 // standalone coefficient sampler.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -103,6 +104,42 @@ static mdp_status check_device() {
 }
 
 // Host action table (Sec. II-A): a = f*Nh + h, theta = 2 pi h/Nh, F = Fmax (f+1)/NF.
+// Per-axis constants of the FP32 landing offset floor(u + d) (see
+// ActionTable): c = floor(d); th = the smallest float >= 1 - frac(d), from
+// the exact FP64 value of 1 - frac(d) (frac(d) of a float has at most 24
+// significant bits; when 1 - frac(d) is not exact in FP64 it lies within
+// 2^-29 of 1 and rounds up to 1 all the same); 2 when frac(d) = 0.
+static void offset_thresholds(const float *d, int A, int32_t *c, float *th, float *T, int32_t *le, int32_t *D) {
+  std::vector<float> u;
+  for (int a = 0; a < A; ++a) {
+    const double dd = (double)d[a];
+    const double fl = std::floor(dd);
+    const double g = dd - fl;   // exact
+    c[a] = (int32_t)fl;
+    if (g == 0.0) {
+      th[a] = 2.0f;
+    } else {
+      const double t1 = 1.0 - g;
+      float f = (float)t1;
+      if ((double)f < t1) f = std::nextafter(f, 2.0f);
+      th[a] = f;
+      u.push_back(f);
+    }
+  }
+  std::sort(u.begin(), u.end());
+  u.erase(std::unique(u.begin(), u.end()), u.end());
+  *D = (int32_t)u.size();
+  for (int i = 0; i < kMaxActions; ++i) T[i] = i < (int)u.size() ? u[i] : 2.0f;
+  for (int a = 0; a < kMaxActions; ++a) {
+    int n = 0;
+    if (a < A)
+      for (float v : u) n += (v <= th[a]) ? 1 : 0;
+    // an integer offset (th = 2) never steps: le = D + 1 exceeds every rank
+    le[a] = (a < A && th[a] < 2.0f) ? n : (int32_t)u.size() + 1;
+  }
+  for (int a = A; a < kMaxActions; ++a) { c[a] = 0; th[a] = 2.0f; }
+}
+
 static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out) {
   if (!ac) return arg_fail("actions is NULL");
   const int A = ac->n_headings * ac->n_speeds;
@@ -131,6 +168,8 @@ static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t
     t->dyl[a] = (float)(dy * lam);
     t->F[a] = (float)F;
   }
+  offset_thresholds(t->dxl, A, t->cx, t->thx, t->Tx, t->lex, &t->Dx);
+  offset_thresholds(t->dyl, A, t->cy, t->thy, t->Ty, t->ley, &t->Dy);
   *A_out = A;
   return MDP_OK;
 }
@@ -384,8 +423,8 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   int chunk = (opts && opts->chunk > 0) ? opts->chunk : 1024;
   if (chunk > N) chunk = N;
   ba.chunk = chunk;
-  int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : 64;
-  if (hist_cap > 4096) return fail(arg_fail("hist_cap must be <= 4096"));
+  int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : 2048;
+  if (hist_cap > 6144) return fail(arg_fail("hist_cap must be <= 6144"));
   uint32_t *defer = nullptr;
   if (prec == MDP_FP32) TRY(dev_alloc((void **)&defer, sizeof(uint32_t) * (size_t)m->n_slices, st));
   ba.cap_bins = hist_cap;

@@ -51,7 +51,7 @@ struct mdp_batch_t {
   unsigned long long *work_d = nullptr;
   BatchSolveItem *sitems_d = nullptr;
   BatchCta *ctas_d = nullptr;
-  int n_ctas = 0, cap_bins = 64, kmax = 0, stage_bytes = 0, max_sweeps_all = 0, cta_threads = 256;
+  int n_ctas = 0, cap_bins = 2048, kmax = 0, stage_bytes = 0, max_sweeps_all = 0, cta_threads = 256;
   size_t cta_smem = 0;
   cudaStream_t st = nullptr;
   cudaGraph_t graph = nullptr;
@@ -180,7 +180,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     }
     mdp_model cm = nullptr;
     mdp_build_opts o{};
-    o.hist_cap = 64;
+    o.hist_cap = 2048;
     const int32_t obj = it.desc.objective;
     mdp_status s = mdp_build(&it.desc.env, &it.desc.grid, &it.desc.actions, it.desc.N, it.desc.subgrid_L,
                              &obj, 1, &o, b->st, &cm);
@@ -197,8 +197,8 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     free_model_on_stream(cm, b->st);
   }
   cudaStreamSynchronize(b->st);
-  // a wider histogram when more than 0.2% of the slices would be deferred
-  b->cap_bins = (wide * 500 > total_slices) ? 128 : 64;
+  // larger fine tables when more than 0.2% of the slices would be deferred
+  b->cap_bins = (wide * 500 > total_slices) ? 4096 : 2048;
   // ---- set-up of every item through the build path, without launching it
   std::vector<BuildArgs> args(n);
   std::vector<int64_t> prefix(n + 1, 0);

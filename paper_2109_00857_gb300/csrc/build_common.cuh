@@ -23,6 +23,15 @@ __device__ __forceinline__ int state_kind(const BuildArgs &a, int64_t s) {
   return KIND_SAMPLE;
 }
 
+// FP32 landing offset along one axis (Sec. II-A move, cell()): floor(u + d)
+// for the exact sum of the floats u and d, as floor(u) + c + [u - floor(u)
+// >= th] with the per-action constants of ActionTable.  Monotone in u, so
+// the offsets of a state's extreme u bound every sample's offset.
+__device__ __forceinline__ int land_offset(float u, int c, float th) {
+  const float n = floorf(u);
+  return (int)n + c + ((u - n) >= th ? 1 : 0);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

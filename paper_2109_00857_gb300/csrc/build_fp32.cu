@@ -8,8 +8,9 @@
 //            edge after the flow, in cells) in shared memory; the per-state
 //            extremes of u bound every landing offset of every action.
 //   phase B  lane l of every warp owns row (state q, action a) = (l / A_pad,
-//            l % A_pad).  For each staged realization it forms
-//            floor(u + d_a dt/dx) in x and y (Sec. II-A move, cell()) and
+//            l % A_pad).  For each staged realization it forms the landing
+//            offset floor(u + d_a dt/dx) in x and y (Sec. II-A move, cell();
+//            land_offset, the floor of the exact sum of the two floats) and
 //            counts the sub-grid bin with a shared-memory reduction into
 //            hist[bin][l]: a lane only ever touches its own bank, so the
 //            counting has no bank or address conflicts within a warp.
@@ -17,15 +18,12 @@
 //            folds out-of-domain / obstacle landings into the sink and forms
 //            R(s,a) from the counts (build_common.cuh).
 // Landing offsets are checked against the sub-grid from the per-state extremes
-// before any count is made (floor and rounded addition are monotone, so the
-// extremes of u give the exact extremes of every action's offsets); a state
+// before any count is made (the offset is monotone in u, so the extremes of u
+// give the exact extremes of every action's offsets); a state
 // whose offsets leave the sub-grid is reported as overflow and counts nothing.
 #include "build_common.cuh"
 
 namespace mdpgb {
-
-constexpr float kMagic = 12582912.0f;         // 1.5 * 2^23: floor via round-down add
-constexpr uint32_t kMagicBits = 0x4B400000u;  // bit pattern of kMagic
 
 __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -72,14 +70,12 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
   // lane role (phase B / emit): row (q_l, a_l) of the slice
   const int q_l = lane / a.A_pad, a_l = lane % a.A_pad;
   const bool act_ok = a_l < a.A;
-  const float dxl = act_ok ? a.act.dxl[a_l] : 0.f;
-  const float dyl = act_ok ? a.act.dyl[a_l] : 0.f;
-  // hist byte address of (bin(fx, fy), lane) for magic-biased floor bits bx, by:
-  //   ((by - M + h) * L + (bx - M + h)) * 128 + lane * 4 + hist_base  (mod 2^32)
+  const int cxl = act_ok ? a.act.cx[a_l] : 0, cyl = act_ok ? a.act.cy[a_l] : 0;
+  const float thxl = act_ok ? a.act.thx[a_l] : 2.f, thyl = act_ok ? a.act.thy[a_l] : 2.f;
+  // hist byte address of (bin(dx, dy), lane): ((dy + h) * L + (dx + h)) * 128 + lane * 4
   const uint32_t rowstride = (uint32_t)a.L * 128u;
   const uint32_t hbase = smem_u32(hist) + (uint32_t)lane * 4u +
-                         ((uint32_t)a.h * (uint32_t)a.L + (uint32_t)a.h) * 128u -
-                         kMagicBits * rowstride - kMagicBits * 128u;
+                         ((uint32_t)a.h * (uint32_t)a.L + (uint32_t)a.h) * 128u;
   // thread role (phase A): state q_t of the slice, realizations w0, w0 + wstride, ...
   const int q_t = tid % a.spw;
   const int w0 = tid / a.spw, wstride = blockDim.x / a.spw;
@@ -180,8 +176,8 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
         run_mnx = fminf(run_mnx, cmnx); run_mxx = fmaxf(run_mxx, cmxx);
         run_mny = fminf(run_mny, cmny); run_mxy = fmaxf(run_mxy, cmxy);
         if (active) {
-          const int lox = (int)floorf(cmnx + dxl), hix = (int)floorf(cmxx + dxl);
-          const int loy = (int)floorf(cmny + dyl), hiy = (int)floorf(cmxy + dyl);
+          const int lox = land_offset(cmnx, cxl, thxl), hix = land_offset(cmxx, cxl, thxl);
+          const int loy = land_offset(cmny, cyl, thyl), hiy = land_offset(cmxy, cyl, thyl);
           if (lox < -a.h || hix > a.h || loy < -a.h || hiy > a.h) active = false;
         }
         // ---- phase B: count landings of this chunk
@@ -190,9 +186,8 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
 #pragma unroll 4
           for (int w = warp; w < cn; w += nwarps) {
             const float2 u = ub[(size_t)w * a.spw];
-            const uint32_t bx = __float_as_uint(__fadd_rd(u.x + dxl, kMagic));
-            const uint32_t by = __float_as_uint(__fadd_rd(u.y + dyl, kMagic));
-            red_add_shared(by * rowstride + bx * 128u + hbase, 1u);
+            const int bx = land_offset(u.x, cxl, thxl), by = land_offset(u.y, cyl, thyl);
+            red_add_shared((uint32_t)by * rowstride + (uint32_t)bx * 128u + hbase, 1u);
           }
         }
         __syncthreads();
@@ -202,8 +197,8 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
     if (warp == 0) {
       int lox = 0, hix = -1, loy = 0, hiy = -1;
       if (kind_l == KIND_SAMPLE && run_mnx <= run_mxx) {
-        lox = (int)floorf(run_mnx + dxl); hix = (int)floorf(run_mxx + dxl);
-        loy = (int)floorf(run_mny + dyl); hiy = (int)floorf(run_mxy + dyl);
+        lox = land_offset(run_mnx, cxl, thxl); hix = land_offset(run_mxx, cxl, thxl);
+        loy = land_offset(run_mny, cyl, thyl); hiy = land_offset(run_mxy, cyl, thyl);
       }
       const bool row_ok = active || kind_l != KIND_SAMPLE;
       if (kind_l == KIND_SAMPLE) {

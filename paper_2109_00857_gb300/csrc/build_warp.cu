@@ -9,11 +9,8 @@ template <int KT, int SPW>
 __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cap = a.cap_bins;
-  uint32_t *hist = smem + (size_t)warp * (cap * 32 + 2 * kItems);
-  float2 *ubuf = reinterpret_cast<float2 *>(hist + cap * 32);   // [spw][CHq]
-  for (int i = lane; i < cap * 32; i += 32) hist[i] = 0;
-  __syncwarp();
+  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * (a.cap_bins + kTab));
+  uint32_t *grid = smem + (size_t)warp * (a.cap_bins + kTab) + kTab;
   WarpAcc acc;
   unsigned long long next = 0;
   if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);
@@ -21,7 +18,7 @@ __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
     const int64_t sl = a.slice_begin + (int64_t)__shfl_sync(0xffffffffu, next, 0);
     if (sl >= a.slice_end) break;
     if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);   // prefetch the next slice
-    warp_slice<KT, SPW>(a, sl, hist, ubuf, acc);
+    warp_slice<KT, SPW>(a, sl, grid, tab, acc);
     __syncwarp();
   }
   warp_flush(a, acc);
@@ -36,10 +33,8 @@ __global__ void __launch_bounds__(256, 3) build_warp_batch_kernel(const BuildArg
                                                                  unsigned long long *work, int cap) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t *hist = smem + (size_t)warp * (cap * 32 + 2 * kItems);
-  float2 *ubuf = reinterpret_cast<float2 *>(hist + cap * 32);
-  for (int i = lane; i < cap * 32; i += 32) hist[i] = 0;
-  __syncwarp();
+  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * (cap + kTab));
+  uint32_t *grid = smem + (size_t)warp * (cap + kTab) + kTab;
   const int64_t total = prefix[n];
   WarpAcc acc;
   int cur = -1;
@@ -58,7 +53,7 @@ __global__ void __launch_bounds__(256, 3) build_warp_batch_kernel(const BuildArg
       if (cur >= 0) warp_flush(items[cur], acc);
       cur = lo;
     }
-    warp_slice<KT, 0>(items[lo], g - prefix[lo], hist, ubuf, acc);
+    warp_slice<KT, 0>(items[lo], g - prefix[lo], grid, tab, acc);
     __syncwarp();
   }
   if (cur >= 0) warp_flush(items[cur], acc);
@@ -68,7 +63,7 @@ template <int KT>
 static cudaError_t launch_wb(const BuildArgs *items_d, const int64_t *prefix_d, int n, unsigned long long *work_d,
                              int cap, cudaStream_t st) {
   const int warps = 8;
-  const size_t smem = ((size_t)cap * 32 + 2 * kItems) * 4 * warps;
+  const size_t smem = ((size_t)cap + kTab) * 4 * warps;
   cudaError_t e = allow_max_smem((const void *)build_warp_batch_kernel<KT>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -90,7 +85,7 @@ cudaError_t launch_build_warp_batch(const BuildArgs *items_d, const int64_t *pre
 
 template <int KT, int SPW>
 static cudaError_t launch_w(const BuildArgs &a, int warps, int sms, cudaStream_t st) {
-  const size_t per_warp = ((size_t)a.cap_bins * 32 + 2 * kItems) * 4;
+  const size_t per_warp = ((size_t)a.cap_bins + kTab) * 4;
   const size_t smem = per_warp * warps;
   cudaError_t e = allow_max_smem((const void *)build_warp_kernel<KT, SPW>);
   if (e != cudaSuccess) return e;

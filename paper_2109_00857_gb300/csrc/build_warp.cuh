@@ -3,35 +3,39 @@
 // batched kernel (batch.cu).
 //
 // A warp works alone on one slice (spw states x A_pad actions, 32 rows) with
-// a private shared-memory histogram and no block-level barrier:
-//   pass 1   lanes form the DO velocity w = vbar + sum_k Y_k v~_k (Sec. II-C)
-//            of (state, realization) items, u = 1/2 + w dt/dx, and reduce the
-//            exact per-state extremes of u over all N realizations.  Floor and
-//            rounded addition are monotone, so floor(ext(u) + d_a dt/dx) is the
-//            exact range of every action's landing offsets: it checks the
-//            neighbouring sub-grid (overflow is an error) and sizes each lane's
-//            histogram to its own bounding box.
-//   pass 2   per chunk of 64 items the lanes stage u in shared memory
-//            (velocity once for all actions), then lane l = (state q, action a)
-//            forms floor(u + d_a dt/dx) in x and y (Sec. II-A move, cell()) and
-//            counts the bin with a shared-memory reduction into hist[bin][l]:
-//            a lane only touches its own bank, so no conflicts.  The counting
-//            loop over a full chunk is unrolled with constant shared offsets.
-//   emit     two scans of each lane's bounding box: count the entries (sink
-//            folded), allocate the slice's columns, then write the entry words
-//            in ascending order with R(s,a) from the counts, zeroing the bins.
-// Slices whose bounding box does not fit cap_bins are appended to a list that
-// the CTA kernel of build_fp32.cu finishes with a full-window histogram; both
-// kernels evaluate u, the floors and R with the same FP32 operations, so a
-// slice's output does not depend on which kernel built it.
+// private shared memory and no block-level barrier.  The landing offset of
+// realization w under action a along x is floor(u_w + d_a) (Sec. II-A move,
+// cell(); u = 1/2 + w dt/dx from the DO velocity, Sec. II-C, d_a the action's
+// displacement), taken for the exact sum of the two floats:
+//   floor(u + d) = floor(u) + c_a + [u - floor(u) >= th_a]
+// with per-action constants c_a, th_a (ActionTable).  Sorting the distinct
+// th_a (T_0 < ... < T_{D-1}) gives each realization one fractional rank
+// rho = #{T <= u - floor(u)} that decides the step for every action at once
+// ([u - floor(u) >= th_a] = [rho >= le_a]).  So a realization needs one count,
+// not one per action:
+//   pass 1   lanes form u for (state, realization) items and reduce the exact
+//            per-state extremes (the offset is monotone in u, so they bound
+//            every action's offsets: sub-grid check, bounding boxes).
+//   pass 2   the same items again: the fine coordinate X = (floor(u) - n0) S +
+//            rho (S = D + 1) per axis, one shared-memory count into the
+//            state's fine table H[X][Y] (sized from the extremes).
+//   prefix   in-place 2-D inclusive prefix sums of H.
+//   emit     lane l = row (state q, action a): an offset bin (dx, dy) collects
+//            exactly the fine cells X in [(dx - c_a - 1 - n0) S + le_a, + S)
+//            (and likewise in y) -- a box whose count is four prefix lookups;
+//            two scans of the row's bounding box count the entries (sink
+//            folded), allocate the slice's columns and write the entry words
+//            in ascending order with R(s,a) from the counts.
+// Slices whose fine tables do not fit cap_bins cells are appended to a list
+// that the CTA kernel of build_fp32.cu finishes with a full-window histogram
+// and the same landing offsets, so a slice's output does not depend on which
+// kernel built it.
 #pragma once
 #include "build_common.cuh"
 
 namespace mdpgb {
 
-constexpr float kMagic = 12582912.0f;         // 1.5 * 2^23: floor via round-down add
-constexpr uint32_t kMagicBits = 0x4B400000u;  // bit pattern of kMagic
-constexpr int kItems = 64;                    // (state, realization) items per chunk per warp
+constexpr int kTab = 128;   // per-warp threshold tables: Tx[64], Ty[64] (padded with 2)
 
 __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -87,18 +91,41 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
   return make_float2(ux, uy);
 }
 
-// Counts one landing: (x, y) = u + d_a rounded to nearest, then floor of both
-// by a round-down add of the magic constant, in packed f32x2 adds (two
-// lanes' worth of FP32 work per instruction, same IEEE results as scalar
-// adds); the floors' bit patterns index the lane's histogram column.
-// u, d: (x, y) pairs as 64-bit registers (x in the low word).
-constexpr unsigned long long kMagic2 = ((unsigned long long)kMagicBits << 32) | kMagicBits;
-__device__ __forceinline__ void count_sample(unsigned long long u, unsigned long long d, uint32_t rowstride,
-                                             uint32_t hb) {
-  unsigned long long p, f;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(u), "l"(d));
-  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(f) : "l"(p), "l"(kMagic2));
-  red_add_shared((uint32_t)(f >> 32) * rowstride + (uint32_t)f * 128u + hb, 1u);
+// #{i : T[i] <= f} for T ascending over its first D entries and padded with
+// 2 to 64 entries; top = the largest power of two <= D (0 when D = 0).
+__device__ __forceinline__ int frac_rank(const float *T, int top, float f) {
+  int r = 0;
+#pragma unroll
+  for (int st = 32; st >= 1; st >>= 1)
+    if (st <= top && T[r + st - 1] <= f) r += st;
+  return r;
+}
+
+// Fine coordinate of u along one axis: (floor(u) - n0) S + rho(u - floor(u)).
+__device__ __forceinline__ int fine_coord(float u, int n0, int S, const float *T, int top) {
+  const float n = floorf(u);
+  return ((int)n - n0) * S + frac_rank(T, top, u - n);
+}
+
+// A state's fine table: X in [xmin, xmin + gx), Y in [ymin, ymin + gy);
+// prefix layout P[i * pitch + j], i <= gx, j <= gy, at word `base` of the
+// warp's table memory (row 0 and column 0 stay zero; pitch is odd, so a
+// warp's lanes walking rows i, i+1, ... hit distinct banks).
+struct FineGeo {
+  int n0x, n0y, xmin, ymin, gx, gy, pitch, base;
+};
+
+__device__ __forceinline__ FineGeo shfl_geo(const FineGeo &g, int src) {
+  FineGeo o;
+  o.n0x = __shfl_sync(0xffffffffu, g.n0x, src);
+  o.n0y = __shfl_sync(0xffffffffu, g.n0y, src);
+  o.xmin = __shfl_sync(0xffffffffu, g.xmin, src);
+  o.ymin = __shfl_sync(0xffffffffu, g.ymin, src);
+  o.gx = __shfl_sync(0xffffffffu, g.gx, src);
+  o.gy = __shfl_sync(0xffffffffu, g.gy, src);
+  o.pitch = __shfl_sync(0xffffffffu, g.pitch, src);
+  o.base = __shfl_sync(0xffffffffu, g.base, src);
+  return o;
 }
 
 // Per-warp totals, added to the model's counters by warp_flush().
@@ -116,32 +143,35 @@ __device__ __forceinline__ void warp_flush(const BuildArgs &a, WarpAcc &acc) {
   acc = WarpAcc();
 }
 
-// One warp builds slice sl of model a: pass 1 (exact extremes), pass 2
-// (counting into hist, sized by the bounding boxes), emit.  hist holds
-// a.cap_bins * 32 zeroed words and is left zeroed; ubuf holds 64 float2.
+// One warp builds slice sl of model a (see the file comment).  grid holds
+// a.cap_bins words of fine-table memory, tab kTab floats.
 // SPW > 0: states per warp fixed at compile time (1: A = 32, 2: A = 16);
 // SPW == 0: runtime spw.  KT: see kPhi.
 template <int KT, int SPW>
-__device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint32_t *hist, float2 *ubuf,
+__device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint32_t *grid, float *tab,
                                            WarpAcc &acc) {
   const int lane = threadIdx.x & 31;
   const int spw = SPW > 0 ? SPW : a.spw;
-  const int CHq = kItems / spw;                    // realizations per state per chunk
   const int K = KT > 0 ? KT : a.K;
-  const int cap = a.cap_bins;
   // lane role: row (q_l, a_l)
   const int q_l = lane / a.A_pad, a_l = lane % a.A_pad;
   const bool act_ok = a_l < a.A;
-  const float dxl = act_ok ? a.act.dxl[a_l] : 0.f;
-  const float dyl = act_ok ? a.act.dyl[a_l] : 0.f;
-  // item role: state q_t, realizations wi and wi + 32/spw of each chunk
+  // item role: state q_t, realizations wi, wi + 32/spw, ...
   const int q_t = lane % spw, wi = lane / spw, wstep = 32 / spw;
   const float lam = a.lam;
   const float *Yall = static_cast<const float *>(a.Y);
   const float *vbar = static_cast<const float *>(a.vbar);
   const float *modes = static_cast<const float *>(a.modes);
-  const uint32_t hist_base = smem_u32(hist) + (uint32_t)lane * 4u;
   const float invN = 1.0f / (float)a.N;
+  float *Tx = tab, *Ty = tab + 64;
+  Tx[lane] = a.act.Tx[lane];
+  Tx[lane + 32] = 2.0f;
+  Ty[lane] = a.act.Ty[lane];
+  Ty[lane + 32] = 2.0f;
+  const int Sx = a.act.Dx + 1, Sy = a.act.Dy + 1;
+  const int topx = a.act.Dx > 0 ? (1 << (31 - __clz(a.act.Dx))) : 0;
+  const int topy = a.act.Dy > 0 ? (1 << (31 - __clz(a.act.Dy))) : 0;
+  __syncwarp();
 
   const int64_t s_l = sl * spw + q_l;
   int kind_l = state_kind(a, s_l);
@@ -151,7 +181,8 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   const bool any_sample = __any_sync(0xffffffffu, kind_t == KIND_SAMPLE);
 
   bool active = kind_l == KIND_SAMPLE;
-  int lox = 0, hix = -1, loy = 0, hiy = -1, pitch = 0;
+  int lox = 0, hix = -1, loy = 0, hiy = -1;
+  FineGeo gl{};   // fine table of state q_l (emit)
   if (any_sample) {
     float phx[kPhi<KT>], phy[kPhi<KT>];
     float vbx = 0.f, vby = 0.f;
@@ -191,72 +222,87 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
       mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, off));
       mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, off));
     }
-    // lane q (q < spw) holds state q's extremes
-    mnx = __shfl_sync(0xffffffffu, mnx, q_l);
-    mxx = __shfl_sync(0xffffffffu, mxx, q_l);
-    mny = __shfl_sync(0xffffffffu, mny, q_l);
-    mxy = __shfl_sync(0xffffffffu, mxy, q_l);
+    // every lane now holds the extremes of its item state q_t; lane q < spw
+    // sizes state q's fine table
+    FineGeo g{};
+    int cells = 0;
+    if (kind_t == KIND_SAMPLE) {
+      g.n0x = (int)floorf(mnx);
+      g.n0y = (int)floorf(mny);
+      g.xmin = fine_coord(mnx, g.n0x, Sx, Tx, topx);
+      g.ymin = fine_coord(mny, g.n0y, Sy, Ty, topy);
+      const long long gx = (long long)fine_coord(mxx, g.n0x, Sx, Tx, topx) - g.xmin + 1;
+      const long long gy = (long long)fine_coord(mxy, g.n0y, Sy, Ty, topy) - g.ymin + 1;
+      const long long pitch = (gy + 1) | 1;
+      const long long c = (gx + 1) * pitch;
+      // a huge spread (only with a sub-grid overflow) cannot be tabled
+      cells = (gx <= 65536 && gy <= 65536 && c <= (long long)a.cap_bins) ? (int)c : a.cap_bins + 1;
+      g.gx = (int)min(gx, 65536LL);
+      g.gy = (int)min(gy, 65536LL);
+      g.pitch = (int)min(pitch, 65537LL);
+    }
+    int total = 0;
+    for (int q = 0; q < spw; ++q) {   // table bases, states in order
+      const int cq = __shfl_sync(0xffffffffu, cells, q);
+      if (lane == q) g.base = total;
+      total += cq;
+    }
+    const FineGeo gt = shfl_geo(g, q_t);
+    gl = shfl_geo(g, q_l);
+    const float lmnx = __shfl_sync(0xffffffffu, mnx, q_l), lmxx = __shfl_sync(0xffffffffu, mxx, q_l);
+    const float lmny = __shfl_sync(0xffffffffu, mny, q_l), lmxy = __shfl_sync(0xffffffffu, mxy, q_l);
+    const int cxa = act_ok ? a.act.cx[a_l] : 0, cya = act_ok ? a.act.cy[a_l] : 0;
+    const float thxa = act_ok ? a.act.thx[a_l] : 2.f, thya = act_ok ? a.act.thy[a_l] : 2.f;
     if (active) {
-      lox = (int)floorf(mnx + dxl); hix = (int)floorf(mxx + dxl);
-      loy = (int)floorf(mny + dyl); hiy = (int)floorf(mxy + dyl);
+      lox = land_offset(lmnx, cxa, thxa); hix = land_offset(lmxx, cxa, thxa);
+      loy = land_offset(lmny, cya, thya); hiy = land_offset(lmxy, cya, thya);
       if (lox < -a.h || hix > a.h || loy < -a.h || hiy > a.h) {   // sub-grid overflow
         active = false;
         atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
       }
     }
-    const int wx = active ? hix - lox + 1 : 0, wy = active ? hiy - loy + 1 : 0;
-    int nrows = wy;
-    pitch = wx;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      pitch = max(pitch, __shfl_xor_sync(0xffffffffu, pitch, off));
-      nrows = max(nrows, __shfl_xor_sync(0xffffffffu, nrows, off));
-    }
-    if (pitch * nrows > cap) {   // too wide for this warp: the CTA kernel builds it
+    if (total > a.cap_bins) {   // too wide for this warp: the CTA kernel builds it
       if (lane == 0) {
         const unsigned long long i = atomicAdd(&a.cnt[CNT_DEFER_N], 1ULL);
         a.defer[i] = (uint32_t)sl;
       }
       return;
     }
-    // ---- pass 2: count
-    const uint32_t rowstride = (uint32_t)pitch * 128u;
-    const uint32_t hb = hist_base - (kMagicBits + (uint32_t)loy) * rowstride -
-                        (kMagicBits + (uint32_t)lox) * 128u;
-    const ulonglong2 *ub4 = reinterpret_cast<const ulonglong2 *>(ubuf + q_l * CHq);
-    const unsigned long long d2 = ((unsigned long long)__float_as_uint(dyl) << 32) | __float_as_uint(dxl);
-    for (int c0 = 0; c0 < a.N; c0 += CHq) {
-      if (kind_t == KIND_SAMPLE) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int wl = wi + j * wstep;
-          const int w = c0 + wl;
-          float2 u = make_float2(0.f, 0.f);
-          if (w < a.N) u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
-          ubuf[q_t * CHq + wl] = u;
+    for (int i = lane; i < total; i += 32) grid[i] = 0;
+    __syncwarp();
+    // ---- pass 2: one count per realization in its state's fine table
+    if (kind_t == KIND_SAMPLE) {
+      const uint32_t gbase = smem_u32(grid + gt.base);
+#pragma unroll 2
+      for (int w = wi; w < a.N; w += wstep) {
+        const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
+        int X = fine_coord(u.x, gt.n0x, Sx, Tx, topx) - gt.xmin;
+        int Y = fine_coord(u.y, gt.n0y, Sy, Ty, topy) - gt.ymin;
+        X = min(max(X, 0), gt.gx - 1);
+        Y = min(max(Y, 0), gt.gy - 1);
+        red_add_shared(gbase + 4u * (uint32_t)((X + 1) * gt.pitch + Y + 1), 1u);
+      }
+    }
+    __syncwarp();
+    // ---- prefix: P[i][j] = sum of H[X'][Y'] over X' < i, Y' < j
+    for (int q = 0; q < spw; ++q) {
+      const FineGeo gq = shfl_geo(g, q);
+      if (gq.gx <= 0 || gq.gy <= 0 || __shfl_sync(0xffffffffu, cells, q) == 0) continue;
+      uint32_t *P = grid + gq.base;
+      for (int i = 1 + lane; i <= gq.gx; i += 32) {
+        uint32_t *row = P + (size_t)i * gq.pitch;
+        uint32_t v = 0;
+        for (int j = 1; j <= gq.gy; ++j) {
+          v += row[j];
+          row[j] = v;
         }
       }
       __syncwarp();
-      if (active) {
-        if (c0 + CHq <= a.N) {
-          if constexpr (SPW > 0) {
-#pragma unroll
-            for (int p = 0; p < kItems / SPW / 2; ++p) {
-              const ulonglong2 u2 = ub4[p];
-              count_sample(u2.x, d2, rowstride, hb);
-              count_sample(u2.y, d2, rowstride, hb);
-            }
-          } else {
-#pragma unroll 4
-            for (int p = 0; p < CHq / 2; ++p) {
-              const ulonglong2 u2 = ub4[p];
-              count_sample(u2.x, d2, rowstride, hb);
-              count_sample(u2.y, d2, rowstride, hb);
-            }
-          }
-        } else {
-          const unsigned long long *ub = reinterpret_cast<const unsigned long long *>(ubuf + q_l * CHq);
-          for (int wl = 0; wl < a.N - c0; ++wl) count_sample(ub[wl], d2, rowstride, hb);
+      for (int j = 1 + lane; j <= gq.gy; j += 32) {
+        uint32_t v = 0;
+        for (int i = 1; i <= gq.gx; ++i) {
+          v += P[(size_t)i * gq.pitch + j];
+          P[(size_t)i * gq.pitch + j] = v;
         }
       }
       __syncwarp();
@@ -264,6 +310,18 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   }
 
   // ---- emit: count entries, allocate the slice, write
+  // count of offset bin (di, dj) of this lane's row: a box of the prefix table
+  const uint32_t *P = grid + gl.base;
+  const int cxa = act_ok ? a.act.cx[a_l] : 0, cya = act_ok ? a.act.cy[a_l] : 0;
+  const int xoff = (-cxa - 1 - gl.n0x) * Sx + (act_ok ? a.act.lex[a_l] : 0) - gl.xmin;
+  const int yoff = (-cya - 1 - gl.n0y) * Sy + (act_ok ? a.act.ley[a_l] : 0) - gl.ymin;
+  auto bin_count = [&](int di, int dj) -> uint32_t {
+    const int x0 = di * Sx + xoff, y0 = dj * Sy + yoff;
+    const int i0 = min(max(x0, 0), gl.gx), i1 = min(max(x0 + Sx, 0), gl.gx);
+    const int j0 = min(max(y0, 0), gl.gy), j1 = min(max(y0 + Sy, 0), gl.gy);
+    const int r0 = i0 * gl.pitch, r1 = i1 * gl.pitch;
+    return P[r1 + j1] - P[r0 + j1] - P[r1 + j0] + P[r0 + j0];
+  };
   const int64_t ir = sl * 32 + lane;
   int e = 0;
   uint32_t sink = 0;
@@ -273,9 +331,8 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   if (kind_l == KIND_SAMPLE && active) {
     for (int dj = loy; dj <= hiy; ++dj) {
       const int jp = cj + dj;
-      const uint32_t *row = hist + (size_t)(dj - loy) * pitch * 32 + lane;
       for (int di = lox; di <= hix; ++di) {
-        const uint32_t n = row[(di - lox) * 32];
+        const uint32_t n = bin_count(di, dj);
         if (n == 0) continue;
         const int ip = ci + di;
         const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
@@ -309,12 +366,9 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     const float g_s = a.gbar ? static_cast<const float *>(a.gbar)[s_l] : 0.f;
     for (int dj = loy; dj <= hiy; ++dj) {
       const int jp = cj + dj;
-      uint32_t *row = hist + (size_t)(dj - loy) * pitch * 32 + lane;
       for (int di = lox; di <= hix; ++di) {
-        uint32_t *hp = row + (di - lox) * 32;
-        const uint32_t n = *hp;
+        const uint32_t n = bin_count(di, dj);
         if (n == 0) continue;
-        *hp = 0;
         const int ip = ci + di;
         const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
         const uint8_t cc = inside ? a.cls[nxt + (int64_t)jp * a.nx + ip] : CLS_OBSTACLE;

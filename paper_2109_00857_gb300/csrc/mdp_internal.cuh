@@ -54,6 +54,18 @@ struct ActionTable {
   double dx64[kMaxActions];  // F cos(theta), F sin(theta), F in FP64 (check mode)
   double dy64[kMaxActions];
   double F64[kMaxActions];
+  // FP32 landing offsets: floor(u + d) of the exact sum of the floats u and
+  // d = floor(u) + c + [u - floor(u) >= th] with c = floor(d) and th the
+  // smallest float >= 1 - (d - c) (2 when d is an integer: never reached).
+  int32_t cx[kMaxActions], cy[kMaxActions];
+  float thx[kMaxActions], thy[kMaxActions];
+  // The distinct thresholds below 2, ascending, padded with 2 (Dx, Dy of
+  // them), and each action's rank le = #{T <= th}: a sample's fractional
+  // rank rho = #{T <= u - floor(u)} decides [u - floor(u) >= th] = [rho >= le]
+  // for every action at once.
+  float Tx[kMaxActions], Ty[kMaxActions];
+  int32_t lex[kMaxActions], ley[kMaxActions];
+  int32_t Dx, Dy;
 };
 
 struct RewardParams {
@@ -81,7 +93,7 @@ struct BuildArgs {
   unsigned long long *cnt;
   int32_t chunk;             // realizations per staged pass (FP32 CTA kernel)
   int64_t slice_begin, slice_end;  // work range [begin, end)
-  int32_t cap_bins;          // per-lane histogram capacity of the warp kernel
+  int32_t cap_bins;          // fine-table words per warp of the warp kernel
   uint32_t *defer;           // slices deferred by the warp kernel ([n_slices])
   const uint32_t *defer_in;  // non-NULL: the CTA kernel works on this list (count CNT_DEFER_N)
 };
@@ -146,7 +158,7 @@ cudaError_t launch_sample_coeffs(int nt, int N, int K, const double *sigma_d, ui
                                  unsigned long long *capped, cudaStream_t st);
 // build
 // warp-per-slice kernel (fast path) followed by the CTA kernel over the
-// slices it deferred (histogram wider than cap_bins)
+// slices it deferred (fine tables larger than cap_bins)
 cudaError_t launch_build_fp32(const BuildArgs &a, int threads, int sms, cudaStream_t st);
 cudaError_t launch_build_warp(const BuildArgs &a, int warps_per_cta, int sms, cudaStream_t st);
 cudaError_t launch_build_fp64(const BuildArgs &a, cudaStream_t st);
