@@ -109,7 +109,8 @@ static mdp_status check_device() {
 // the exact FP64 value of 1 - frac(d) (frac(d) of a float has at most 24
 // significant bits; when 1 - frac(d) is not exact in FP64 it lies within
 // 2^-29 of 1 and rounds up to 1 all the same); 2 when frac(d) = 0.
-static void offset_thresholds(const float *d, int A, int32_t *c, float *th, float *T, int32_t *le, int32_t *D) {
+static void offset_thresholds(const float *d, int A, int32_t *c, float *th, float *T, int32_t *le, int32_t *D,
+                              uint32_t *L) {
   std::vector<float> u;
   for (int a = 0; a < A; ++a) {
     const double dd = (double)d[a];
@@ -138,6 +139,14 @@ static void offset_thresholds(const float *d, int A, int32_t *c, float *th, floa
     le[a] = (a < A && th[a] < 2.0f) ? n : (int32_t)u.size() + 1;
   }
   for (int a = A; a < kMaxActions; ++a) { c[a] = 0; th[a] = 2.0f; }
+  // rank lookup: thresholds bucketed by floor(128 T) (clamped to the last bucket)
+  std::vector<int> inb(kRankBuckets, 0);
+  for (float v : u) inb[std::min((int)std::floor((double)v * kRankBuckets), kRankBuckets - 1)]++;
+  int below = 0;
+  for (int b = 0; b < kRankBuckets; ++b) {
+    L[b] = (uint32_t)below | ((uint32_t)inb[b] << 8);
+    below += inb[b];
+  }
 }
 
 static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out) {
@@ -168,8 +177,8 @@ static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t
     t->dyl[a] = (float)(dy * lam);
     t->F[a] = (float)F;
   }
-  offset_thresholds(t->dxl, A, t->cx, t->thx, t->Tx, t->lex, &t->Dx);
-  offset_thresholds(t->dyl, A, t->cy, t->thy, t->Ty, t->ley, &t->Dy);
+  offset_thresholds(t->dxl, A, t->cx, t->thx, t->Tx, t->lex, &t->Dx, t->Lx);
+  offset_thresholds(t->dyl, A, t->cy, t->thy, t->Ty, t->ley, &t->Dy, t->Ly);
   *A_out = A;
   return MDP_OK;
 }

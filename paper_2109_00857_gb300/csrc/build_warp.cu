@@ -11,6 +11,7 @@ __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *tab = reinterpret_cast<float *>(smem + (size_t)warp * (a.cap_bins + kTab));
   uint32_t *grid = smem + (size_t)warp * (a.cap_bins + kTab) + kTab;
+  load_rank_tables(a, tab);
   WarpAcc acc;
   unsigned long long next = 0;
   if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);
@@ -52,6 +53,8 @@ __global__ void __launch_bounds__(256, 3) build_warp_batch_kernel(const BuildArg
     if (lo != cur) {
       if (cur >= 0) warp_flush(items[cur], acc);
       cur = lo;
+      __syncwarp();
+      load_rank_tables(items[lo], tab);
     }
     warp_slice<KT, 0>(items[lo], g - prefix[lo], grid, tab, acc);
     __syncwarp();

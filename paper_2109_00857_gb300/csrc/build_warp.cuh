@@ -35,7 +35,8 @@
 
 namespace mdpgb {
 
-constexpr int kTab = 128;   // per-warp threshold tables: Tx[64], Ty[64] (padded with 2)
+// per-warp rank tables: Tx[32], Ty[32], Lx[kRankBuckets], Ly[kRankBuckets]
+constexpr int kTab = 64 + 2 * kRankBuckets;
 
 __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -91,20 +92,34 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
   return make_float2(ux, uy);
 }
 
-// #{i : T[i] <= f} for T ascending over its first D entries and padded with
-// 2 to 64 entries; top = the largest power of two <= D (0 when D = 0).
-__device__ __forceinline__ int frac_rank(const float *T, int top, float f) {
-  int r = 0;
-#pragma unroll
-  for (int st = 32; st >= 1; st >>= 1)
-    if (st <= top && T[r + st - 1] <= f) r += st;
+// #{i : T[i] <= f} for f in [0, 1]: the bucket entry gives the thresholds
+// below f's bucket and how many lie inside it (usually 0 or 1), which are
+// compared one by one.
+__device__ __forceinline__ int frac_rank(const float *T, const uint32_t *L, float f) {
+  const uint32_t e = L[min((int)(f * (float)kRankBuckets), kRankBuckets - 1)];
+  const int first = (int)(e & 0xFFu), n = (int)(e >> 8);
+  int r = first;
+  for (int i = 0; i < n; ++i) r += (T[first + i] <= f) ? 1 : 0;
   return r;
 }
 
 // Fine coordinate of u along one axis: (floor(u) - n0) S + rho(u - floor(u)).
-__device__ __forceinline__ int fine_coord(float u, int n0, int S, const float *T, int top) {
+__device__ __forceinline__ int fine_coord(float u, int n0, int S, const float *T, const uint32_t *L) {
   const float n = floorf(u);
-  return ((int)n - n0) * S + frac_rank(T, top, u - n);
+  return ((int)n - n0) * S + frac_rank(T, L, u - n);
+}
+
+// Copies a model's rank tables into a warp's table memory (whole warp).
+__device__ __forceinline__ void load_rank_tables(const BuildArgs &a, float *tab) {
+  const int lane = threadIdx.x & 31;
+  uint32_t *L = reinterpret_cast<uint32_t *>(tab + 64);
+  tab[lane] = a.act.Tx[lane];
+  tab[32 + lane] = a.act.Ty[lane];
+  for (int b = lane; b < kRankBuckets; b += 32) {
+    L[b] = a.act.Lx[b];
+    L[kRankBuckets + b] = a.act.Ly[b];
+  }
+  __syncwarp();
 }
 
 // A state's fine table: X in [xmin, xmin + gx), Y in [ymin, ymin + gy);
@@ -144,7 +159,8 @@ __device__ __forceinline__ void warp_flush(const BuildArgs &a, WarpAcc &acc) {
 }
 
 // One warp builds slice sl of model a (see the file comment).  grid holds
-// a.cap_bins words of fine-table memory, tab kTab floats.
+// a.cap_bins words of fine-table memory, tab the model's rank tables
+// (kTab words, filled by load_rank_tables).
 // SPW > 0: states per warp fixed at compile time (1: A = 32, 2: A = 16);
 // SPW == 0: runtime spw.  KT: see kPhi.
 template <int KT, int SPW>
@@ -163,15 +179,9 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   const float *vbar = static_cast<const float *>(a.vbar);
   const float *modes = static_cast<const float *>(a.modes);
   const float invN = 1.0f / (float)a.N;
-  float *Tx = tab, *Ty = tab + 64;
-  Tx[lane] = a.act.Tx[lane];
-  Tx[lane + 32] = 2.0f;
-  Ty[lane] = a.act.Ty[lane];
-  Ty[lane + 32] = 2.0f;
+  const float *Tx = tab, *Ty = tab + 32;   // rank tables (load_rank_tables)
+  const uint32_t *Lx = reinterpret_cast<const uint32_t *>(tab + 64), *Ly = Lx + kRankBuckets;
   const int Sx = a.act.Dx + 1, Sy = a.act.Dy + 1;
-  const int topx = a.act.Dx > 0 ? (1 << (31 - __clz(a.act.Dx))) : 0;
-  const int topy = a.act.Dy > 0 ? (1 << (31 - __clz(a.act.Dy))) : 0;
-  __syncwarp();
 
   const int64_t s_l = sl * spw + q_l;
   int kind_l = state_kind(a, s_l);
@@ -229,10 +239,10 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     if (kind_t == KIND_SAMPLE) {
       g.n0x = (int)floorf(mnx);
       g.n0y = (int)floorf(mny);
-      g.xmin = fine_coord(mnx, g.n0x, Sx, Tx, topx);
-      g.ymin = fine_coord(mny, g.n0y, Sy, Ty, topy);
-      const long long gx = (long long)fine_coord(mxx, g.n0x, Sx, Tx, topx) - g.xmin + 1;
-      const long long gy = (long long)fine_coord(mxy, g.n0y, Sy, Ty, topy) - g.ymin + 1;
+      g.xmin = fine_coord(mnx, g.n0x, Sx, Tx, Lx);
+      g.ymin = fine_coord(mny, g.n0y, Sy, Ty, Ly);
+      const long long gx = (long long)fine_coord(mxx, g.n0x, Sx, Tx, Lx) - g.xmin + 1;
+      const long long gy = (long long)fine_coord(mxy, g.n0y, Sy, Ty, Ly) - g.ymin + 1;
       const long long pitch = (gy + 1) | 1;
       const long long c = (gx + 1) * pitch;
       // a huge spread (only with a sub-grid overflow) cannot be tabled
@@ -273,11 +283,11 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     // ---- pass 2: one count per realization in its state's fine table
     if (kind_t == KIND_SAMPLE) {
       const uint32_t gbase = smem_u32(grid + gt.base);
-#pragma unroll 2
+#pragma unroll 1
       for (int w = wi; w < a.N; w += wstep) {
         const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
-        int X = fine_coord(u.x, gt.n0x, Sx, Tx, topx) - gt.xmin;
-        int Y = fine_coord(u.y, gt.n0y, Sy, Ty, topy) - gt.ymin;
+        int X = fine_coord(u.x, gt.n0x, Sx, Tx, Lx) - gt.xmin;
+        int Y = fine_coord(u.y, gt.n0y, Sy, Ty, Ly) - gt.ymin;
         X = min(max(X, 0), gt.gx - 1);
         Y = min(max(Y, 0), gt.gy - 1);
         red_add_shared(gbase + 4u * (uint32_t)((X + 1) * gt.pitch + Y + 1), 1u);

@@ -47,6 +47,8 @@ enum {
   CNT_N = 16
 };
 
+constexpr int kRankBuckets = 128;
+
 struct ActionTable {
   float dxl[kMaxActions];   // F cos(theta) * dt/dx   (FP32 kinematics, grid units)
   float dyl[kMaxActions];
@@ -66,6 +68,10 @@ struct ActionTable {
   float Tx[kMaxActions], Ty[kMaxActions];
   int32_t lex[kMaxActions], ley[kMaxActions];
   int32_t Dx, Dy;
+  // Rank lookup over kRankBuckets equal buckets of [0, 1]: entry b =
+  // #{T in buckets < b} | (#{T in bucket b} << 8), bucket(v) =
+  // min(floor(128 v), 127) (exact: 128 is a power of two).
+  uint32_t Lx[kRankBuckets], Ly[kRankBuckets];
 };
 
 struct RewardParams {
