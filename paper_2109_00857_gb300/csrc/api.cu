@@ -110,17 +110,18 @@ static mdp_status check_device() {
 // significant bits; when 1 - frac(d) is not exact in FP64 it lies within
 // 2^-29 of 1 and rounds up to 1 all the same); 2 when frac(d) = 0.
 static void offset_thresholds(const float *d, int A, int32_t *c, float *th, float *T, int32_t *le, int32_t *D,
-                              uint32_t *L) {
+                              uint8_t *L, int32_t *M) {
   std::vector<float> u;
   for (int a = 0; a < A; ++a) {
     const double dd = (double)d[a];
     const double fl = std::floor(dd);
-    const double g = dd - fl;   // exact
     c[a] = (int32_t)fl;
-    if (g == 0.0) {
+    if (dd == fl) {
       th[a] = 2.0f;
     } else {
-      const double t1 = 1.0 - g;
+      // 1 - frac(d) = (floor(d) + 1) - d, exact in FP64 unless 0 < d < 2^-29
+      // (then it lies within 2^-29 of 1 and rounds up to 1 either way)
+      const double t1 = (fl + 1.0) - dd;
       float f = (float)t1;
       if ((double)f < t1) f = std::nextafter(f, 2.0f);
       th[a] = f;
@@ -130,7 +131,7 @@ static void offset_thresholds(const float *d, int A, int32_t *c, float *th, floa
   std::sort(u.begin(), u.end());
   u.erase(std::unique(u.begin(), u.end()), u.end());
   *D = (int32_t)u.size();
-  for (int i = 0; i < kMaxActions; ++i) T[i] = i < (int)u.size() ? u[i] : 2.0f;
+  for (int i = 0; i < kMaxActions + 2; ++i) T[i] = i < (int)u.size() ? u[i] : 2.0f;
   for (int a = 0; a < kMaxActions; ++a) {
     int n = 0;
     if (a < A)
@@ -143,9 +144,11 @@ static void offset_thresholds(const float *d, int A, int32_t *c, float *th, floa
   std::vector<int> inb(kRankBuckets, 0);
   for (float v : u) inb[std::min((int)std::floor((double)v * kRankBuckets), kRankBuckets - 1)]++;
   int below = 0;
+  *M = 0;
   for (int b = 0; b < kRankBuckets; ++b) {
-    L[b] = (uint32_t)below | ((uint32_t)inb[b] << 8);
+    L[b] = (uint8_t)below;
     below += inb[b];
+    *M = std::max(*M, inb[b]);
   }
 }
 
@@ -177,8 +180,8 @@ static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t
     t->dyl[a] = (float)(dy * lam);
     t->F[a] = (float)F;
   }
-  offset_thresholds(t->dxl, A, t->cx, t->thx, t->Tx, t->lex, &t->Dx, t->Lx);
-  offset_thresholds(t->dyl, A, t->cy, t->thy, t->Ty, t->ley, &t->Dy, t->Ly);
+  offset_thresholds(t->dxl, A, t->cx, t->thx, t->Tx, t->lex, &t->Dx, t->Lx, &t->Mx);
+  offset_thresholds(t->dyl, A, t->cy, t->thy, t->Ty, t->ley, &t->Dy, t->Ly, &t->My);
   *A_out = A;
   return MDP_OK;
 }

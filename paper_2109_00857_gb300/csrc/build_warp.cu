@@ -9,8 +9,8 @@ template <int KT, int SPW>
 __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * (a.cap_bins + kTab));
-  uint32_t *grid = smem + (size_t)warp * (a.cap_bins + kTab) + kTab;
+  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * warp_words(a.cap_bins));
+  uint32_t *grid = smem + (size_t)warp * warp_words(a.cap_bins) + kTab;
   load_rank_tables(a, tab);
   WarpAcc acc;
   unsigned long long next = 0;
@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(256, 3) build_warp_batch_kernel(const BuildArg
                                                                  unsigned long long *work, int cap) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * (cap + kTab));
-  uint32_t *grid = smem + (size_t)warp * (cap + kTab) + kTab;
+  float *tab = reinterpret_cast<float *>(smem + (size_t)warp * warp_words(cap));
+  uint32_t *grid = smem + (size_t)warp * warp_words(cap) + kTab;
   const int64_t total = prefix[n];
   WarpAcc acc;
   int cur = -1;
@@ -66,7 +66,7 @@ template <int KT>
 static cudaError_t launch_wb(const BuildArgs *items_d, const int64_t *prefix_d, int n, unsigned long long *work_d,
                              int cap, cudaStream_t st) {
   const int warps = 8;
-  const size_t smem = ((size_t)cap + kTab) * 4 * warps;
+  const size_t smem = (size_t)warp_words(cap) * 4 * warps;
   cudaError_t e = allow_max_smem((const void *)build_warp_batch_kernel<KT>);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -88,7 +88,7 @@ cudaError_t launch_build_warp_batch(const BuildArgs *items_d, const int64_t *pre
 
 template <int KT, int SPW>
 static cudaError_t launch_w(const BuildArgs &a, int warps, int sms, cudaStream_t st) {
-  const size_t per_warp = ((size_t)a.cap_bins + kTab) * 4;
+  const size_t per_warp = (size_t)warp_words(a.cap_bins) * 4;
   const size_t smem = per_warp * warps;
   cudaError_t e = allow_max_smem((const void *)build_warp_kernel<KT, SPW>);
   if (e != cudaSuccess) return e;

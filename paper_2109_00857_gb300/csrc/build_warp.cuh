@@ -35,8 +35,14 @@
 
 namespace mdpgb {
 
-// per-warp rank tables: Tx[32], Ty[32], Lx[kRankBuckets], Ly[kRankBuckets]
-constexpr int kTab = 64 + 2 * kRankBuckets;
+// per-warp rank tables (32-bit words): TPx[33], TPy[33] as float2 pairs
+// (T[i], T[i+1]), then Lx, Ly as bytes
+constexpr int kTabPairs = kMaxActions + 1;
+constexpr int kTab = 4 * kTabPairs + 2 * kRankBuckets / 4 + 2;   // even: float2 alignment kept
+
+// Shared-memory words per warp: rank tables + fine tables, a multiple of 4
+// so every warp's tables start 16-byte aligned.
+__host__ __device__ constexpr int warp_words(int cap) { return (kTab + cap + 3) & ~3; }
 
 __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -92,34 +98,53 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
   return make_float2(ux, uy);
 }
 
-// #{i : T[i] <= f} for f in [0, 1]: the bucket entry gives the thresholds
-// below f's bucket and how many lie inside it (usually 0 or 1), which are
-// compared one by one.
-__device__ __forceinline__ int frac_rank(const float *T, const uint32_t *L, float f) {
-  const uint32_t e = L[min((int)(f * (float)kRankBuckets), kRankBuckets - 1)];
-  const int first = (int)(e & 0xFFu), n = (int)(e >> 8);
-  int r = first;
-  for (int i = 0; i < n; ++i) r += (T[first + i] <= f) ? 1 : 0;
+// Rank tables of one axis in a warp's table memory.
+struct RankTab {
+  const float2 *TP;    // TP[i] = (T[i], T[i+1]); T[i] = 2 for i >= D
+  const uint8_t *L;    // thresholds below each bucket
+  int M;               // most thresholds in one bucket
+};
+
+// #{i : T[i] <= f} for f in [0, 1].  The thresholds below f's bucket come
+// from the lookup; those in the bucket follow them in T, and every later
+// one exceeds f, so with at most two per bucket two comparisons finish it.
+__device__ __forceinline__ int frac_rank(const RankTab &rt, float f) {
+  int r = rt.L[min((int)(f * (float)kRankBuckets), kRankBuckets - 1)];
+  if (rt.M <= 2) {
+    const float2 t = rt.TP[r];
+    return r + (t.x <= f ? 1 : 0) + (t.y <= f ? 1 : 0);
+  }
+  while (rt.TP[r].x <= f) ++r;   // T[D] = 2 > f ends it
   return r;
 }
 
 // Fine coordinate of u along one axis: (floor(u) - n0) S + rho(u - floor(u)).
-__device__ __forceinline__ int fine_coord(float u, int n0, int S, const float *T, const uint32_t *L) {
+__device__ __forceinline__ int fine_coord(float u, int n0, int S, const RankTab &rt) {
   const float n = floorf(u);
-  return ((int)n - n0) * S + frac_rank(T, L, u - n);
+  return ((int)n - n0) * S + frac_rank(rt, u - n);
 }
 
 // Copies a model's rank tables into a warp's table memory (whole warp).
 __device__ __forceinline__ void load_rank_tables(const BuildArgs &a, float *tab) {
   const int lane = threadIdx.x & 31;
-  uint32_t *L = reinterpret_cast<uint32_t *>(tab + 64);
-  tab[lane] = a.act.Tx[lane];
-  tab[32 + lane] = a.act.Ty[lane];
+  float2 *TPx = reinterpret_cast<float2 *>(tab), *TPy = TPx + kTabPairs;
+  uint8_t *L = reinterpret_cast<uint8_t *>(TPy + kTabPairs);
+  for (int i = lane; i < kTabPairs; i += 32) {
+    TPx[i] = make_float2(a.act.Tx[i], a.act.Tx[i + 1]);
+    TPy[i] = make_float2(a.act.Ty[i], a.act.Ty[i + 1]);
+  }
   for (int b = lane; b < kRankBuckets; b += 32) {
     L[b] = a.act.Lx[b];
     L[kRankBuckets + b] = a.act.Ly[b];
   }
   __syncwarp();
+}
+
+__device__ __forceinline__ RankTab rank_tab(const BuildArgs &a, const float *tab, int axis) {
+  const float2 *TP = reinterpret_cast<const float2 *>(tab) + axis * kTabPairs;
+  const uint8_t *L = reinterpret_cast<const uint8_t *>(reinterpret_cast<const float2 *>(tab) + 2 * kTabPairs) +
+                     axis * kRankBuckets;
+  return RankTab{TP, L, axis ? a.act.My : a.act.Mx};
 }
 
 // A state's fine table: X in [xmin, xmin + gx), Y in [ymin, ymin + gy);
@@ -179,8 +204,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   const float *vbar = static_cast<const float *>(a.vbar);
   const float *modes = static_cast<const float *>(a.modes);
   const float invN = 1.0f / (float)a.N;
-  const float *Tx = tab, *Ty = tab + 32;   // rank tables (load_rank_tables)
-  const uint32_t *Lx = reinterpret_cast<const uint32_t *>(tab + 64), *Ly = Lx + kRankBuckets;
+  const RankTab rx = rank_tab(a, tab, 0), ry = rank_tab(a, tab, 1);   // (load_rank_tables)
   const int Sx = a.act.Dx + 1, Sy = a.act.Dy + 1;
 
   const int64_t s_l = sl * spw + q_l;
@@ -239,10 +263,10 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     if (kind_t == KIND_SAMPLE) {
       g.n0x = (int)floorf(mnx);
       g.n0y = (int)floorf(mny);
-      g.xmin = fine_coord(mnx, g.n0x, Sx, Tx, Lx);
-      g.ymin = fine_coord(mny, g.n0y, Sy, Ty, Ly);
-      const long long gx = (long long)fine_coord(mxx, g.n0x, Sx, Tx, Lx) - g.xmin + 1;
-      const long long gy = (long long)fine_coord(mxy, g.n0y, Sy, Ty, Ly) - g.ymin + 1;
+      g.xmin = fine_coord(mnx, g.n0x, Sx, rx);
+      g.ymin = fine_coord(mny, g.n0y, Sy, ry);
+      const long long gx = (long long)fine_coord(mxx, g.n0x, Sx, rx) - g.xmin + 1;
+      const long long gy = (long long)fine_coord(mxy, g.n0y, Sy, ry) - g.ymin + 1;
       const long long pitch = (gy + 1) | 1;
       const long long c = (gx + 1) * pitch;
       // a huge spread (only with a sub-grid overflow) cannot be tabled
@@ -286,8 +310,8 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
 #pragma unroll 1
       for (int w = wi; w < a.N; w += wstep) {
         const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
-        int X = fine_coord(u.x, gt.n0x, Sx, Tx, Lx) - gt.xmin;
-        int Y = fine_coord(u.y, gt.n0y, Sy, Ty, Ly) - gt.ymin;
+        int X = fine_coord(u.x, gt.n0x, Sx, rx) - gt.xmin;
+        int Y = fine_coord(u.y, gt.n0y, Sy, ry) - gt.ymin;
         X = min(max(X, 0), gt.gx - 1);
         Y = min(max(Y, 0), gt.gy - 1);
         red_add_shared(gbase + 4u * (uint32_t)((X + 1) * gt.pitch + Y + 1), 1u);

@@ -65,13 +65,14 @@ struct ActionTable {
   // them), and each action's rank le = #{T <= th}: a sample's fractional
   // rank rho = #{T <= u - floor(u)} decides [u - floor(u) >= th] = [rho >= le]
   // for every action at once.
-  float Tx[kMaxActions], Ty[kMaxActions];
+  float Tx[kMaxActions + 2], Ty[kMaxActions + 2];
   int32_t lex[kMaxActions], ley[kMaxActions];
   int32_t Dx, Dy;
   // Rank lookup over kRankBuckets equal buckets of [0, 1]: entry b =
-  // #{T in buckets < b} | (#{T in bucket b} << 8), bucket(v) =
-  // min(floor(128 v), 127) (exact: 128 is a power of two).
-  uint32_t Lx[kRankBuckets], Ly[kRankBuckets];
+  // #{T in buckets < b}, bucket(v) = min(floor(128 v), 127) (exact: 128 is a
+  // power of two); Mx, My = most thresholds in one bucket.
+  uint8_t Lx[kRankBuckets], Ly[kRankBuckets];
+  int32_t Mx, My;
 };
 
 struct RewardParams {
