@@ -54,12 +54,22 @@ def workload(name, rank=0, nt=None):
     return env
 
 
-def algorithmic_ops_per_sample(env):
-    """Issue-slot count the method itself needs per landing sample: 2 adds
-    (x + (v + a) dt in cell units, per coordinate), 2 floors (cell()), 1 bin
-    index, 1 count; plus the velocity synthesis 2K FMAs + 2 scalings per
-    (state, realization) shared by the A actions."""
-    return 6.0 + (2.0 * env.K + 2.0) / env.A
+def kernel_counters(kernel, workload_name):
+    """ncu per-unit counters of a kernel (profiles/counters.json), or None when
+    the kernel's sources changed since the capture or the workload differs."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
+            c = json.load(f)[kernel]
+        h = hashlib.sha256()
+        for src in c["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != c["sha256"] or not workload_name.startswith(c.get("workload", "large")):
+            return None
+        return c
+    except Exception:
+        return None
 
 
 def bellman_bytes_per_sweep(info, nS, n_obj=1):
@@ -426,11 +436,14 @@ def main():
     hbm, sm_mhz, peak_kind = peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
 
-    # build kernel (dominant) against the issue-slot roofline
-    ops = algorithmic_ops_per_sample(env)
+    # build kernel against the issue-slot roofline: ncu warp instructions per
+    # slice x slices per launch / launch time, against one warp instruction
+    # per SM sub-partition per cycle (SMs x 4 x sm_max_mhz)
     kmean = statistics.mean(kern_ms)
-    build_achieved = info.samples * ops / (kmean / 1e3) / 1e12      # Tops/s
-    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12
+    n_slices = -(-env.nS // (32 // max(1, 1 << (env.A - 1).bit_length())))
+    cb = kernel_counters("build_warp_kernel", env.name)
+    issue_peak = sms * 4 * sm_mhz * 1e6 / 1e12                      # T warp-inst/s
+    build_achieved = cb["warp_inst_per_unit"] * n_slices / (kmean / 1e3) / 1e12 if cb else None
     # Bellman sweep against HBM
     n_fused = 1 if args.separate else len(objs)
     bpsw = bellman_bytes_per_sweep(info, env.nS, n_fused)
@@ -438,15 +451,22 @@ def main():
     # sweeps recomputed; layered: one pass = one sweep's work)
     sweep_ms = sum(solve_ms) / max(full_equiv, 1e-9)
     bell_achieved = bpsw / (sweep_ms / 1e3) / 1e9
-    roof_build = {"kernel": "build_warp_kernel (+ build_fp32_kernel on wide slices)", "bound": "alu", "achieved": build_achieved,
-                  "peak": alu_peak, "unit": "Tops/s", "frac": build_achieved / alu_peak,
-                  "traffic": None,
-                  "ops_per_sample": ops, "ms_per_launch": kmean,
-                  "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
+    cs = kernel_counters("bellman_kernel_fused3", env.name) if n_fused == 3 else None
+    roof_build = {"kernel": "build_warp_kernel (+ build_fp32_kernel on wide slices)", "bound": "alu",
+                  "achieved": build_achieved, "peak": issue_peak, "unit": "T warp-inst/s",
+                  "frac": build_achieved / issue_peak if cb else None,
+                  "traffic": cb["dram_bytes_per_unit"] * n_slices if cb else None,
+                  "units_per_launch": n_slices,
+                  "warp_inst_per_unit": cb["warp_inst_per_unit"] if cb else None,
+                  "counters": cb["summary"] if cb else "stale or absent: kernel changed since the capture",
+                  "ms_per_launch": kmean,
+                  "peak_basis": f"{sms} SMs x 4 issue slots x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
     roof_bell = {"kernel": "bellman_kernel", "objectives_per_sweep": n_fused, "bound": "hbm",
                  "achieved": bell_achieved, "peak": hbm, "unit": "GB/s", "frac": bell_achieved / hbm,
-                 "traffic": None, "bytes_per_sweep": bpsw, "ms_per_sweep": sweep_ms,
+                 "traffic": cs["dram_bytes_per_unit"] * n_slices if cs else None,
+                 "bytes_per_sweep": bpsw, "ms_per_sweep": sweep_ms,
                  "full_sweep_equivalents_per_solve": full_equiv / args.steps,
+                 "counters": cs["summary"] if cs else "stale or absent",
                  "peak_basis": f"hbm_gbs ({peak_kind})"}
     build_share = sum(kern_ms) / t_ms
     solve_share = sum(solve_ms) / t_ms

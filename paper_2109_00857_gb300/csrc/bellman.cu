@@ -127,7 +127,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 }
 
 constexpr int kWarps = 8;     // warps per CTA
-constexpr int kDepth = 3;     // slices each warp keeps in flight
+constexpr int kDepth = 2;     // slices each warp keeps in flight
 
 struct PipeRange {
   int64_t sl_lo, sl_hi;   // slices of this launch
