@@ -92,7 +92,9 @@ typedef struct {
 } mdp_actions;
 
 /* Environment data (Alg. 1 inputs: vbar, v~_i, mu_i, gbar, m).  Element type of
- * every floating array is float for MDP_FP32 and double for MDP_FP64_CHECK. */
+ * every floating array is float for MDP_FP32 and double for MDP_FP64_CHECK.
+ * Alignment: vbar and modes to one (x, y) pair (8 B FP32, 16 B FP64), coeffs
+ * to 16 B, gbar to 4 B; otherwise mdp_build returns MDP_ERR_ARG. */
 typedef struct {
   int32_t K;               /* number of DO modes, 0..16 */
   int32_t precision;       /* mdp_precision */

@@ -25,6 +25,7 @@ UNITS = {
     "api.cu": [],
     "build_fp32.cu": [],
     "build_warp.cu": [],
+    "build_warp_batch.cu": [],
     "bellman.cu": [],
     "serve.cu": [],
     "noalloc.cu": [],

@@ -283,6 +283,11 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   if (!env->vbar || !env->obstacle || !env->target || (env->K > 0 && !env->modes))
     return arg_fail("vbar, modes, obstacle and target must be non-NULL");
   if (env->K > 0 && !env->coeffs && !env->sigma_h) return arg_fail("need coeffs or sigma_h");
+  // the kernels load (x, y) pairs and coefficient rows as vectors
+  if (((uintptr_t)env->vbar | (uintptr_t)env->modes) & (2 * (env->precision == MDP_FP64_CHECK ? 8 : 4) - 1))
+    return arg_fail("vbar and modes must be aligned to one (x, y) pair");
+  if ((uintptr_t)env->coeffs & 15) return arg_fail("coeffs must be 16-byte aligned");
+  if ((uintptr_t)env->gbar & 3) return arg_fail("gbar must be 4-byte aligned");
   if (subgrid_L < 0 || subgrid_L > 255 || (subgrid_L > 0 && subgrid_L % 2 == 0))
     return arg_fail("subgrid_L must be 0 (auto) or odd in [1, 255]");
   const int row_cap = (opts && opts->row_cap > 0) ? opts->row_cap : 64;

@@ -9,10 +9,12 @@
 // sizes the Bellman stages for the widest slice.  Then each item is set up
 // through the same path as mdp_build (allocations, coefficient table, cell
 // classes) without launching its build.
-// Run: one persistent warp-per-slice launch builds every item's slices from
-// one global work queue; one CTA launch finishes the slices any item deferred;
+// Run: one persistent warp-per-slice launch per states-per-warp class
+// builds its items' slices from one work queue; one CTA launch finishes the
+// slices any item deferred;
 // each Jacobi sweep is one launch over all items (CTAs own contiguous slice
-// ranges of one item; an item stops on its own residual); one launch
+// ranges of one item, narrowed in-kernel to the layers whose inputs changed
+// in the previous sweep; an item stops on its own residual); one launch
 // finalizes all.  The whole sequence (with the per-item coefficient draws,
 // cell classes, clears and the status copies) is captured once into a CUDA
 // graph and replayed on every run.
@@ -33,6 +35,7 @@ struct Item {
   mdp_model_t *m = nullptr;
   BuildHook hook;
   float *Vb = nullptr;
+  uint8_t *lflags = nullptr;   // active-layer sweep flags, 3 x (nt + 1)
   unsigned long long *res = nullptr;
   double *stats = nullptr;
   int max_sweeps = 0;
@@ -52,6 +55,12 @@ struct mdp_batch_t {
   BatchSolveItem *sitems_d = nullptr;
   BatchCta *ctas_d = nullptr;
   int n_ctas = 0, cap_bins = 2048, kmax = 0, stage_bytes = 0, max_sweeps_all = 0, cta_threads = 256;
+  // build launches: items grouped by (states per warp, mode count), each
+  // group one persistent launch over its own zero-based prefix segment
+  struct Group {
+    int start, n, pstart, K, spw;
+  };
+  std::vector<Group> groups;
   size_t cta_smem = 0;
   cudaStream_t st = nullptr;
   cudaGraph_t graph = nullptr;
@@ -74,6 +83,7 @@ void batch_release(mdp_batch_t *b) {
     dev_free(it.hook.sigma_d, b->st);
     dev_free(it.hook.defer, b->st);
     dev_free(it.Vb, b->st);
+    dev_free(it.lflags, b->st);
     dev_free(it.res, b->st);
     dev_free(it.stats, b->st);
   }
@@ -94,7 +104,7 @@ void batch_release(mdp_batch_t *b) {
 // Every stream operation of one run, in order (captured into the graph).
 cudaError_t enqueue(mdp_batch_t *b) {
   cudaStream_t st = b->st;
-  cudaError_t e = cudaMemsetAsync(b->work_d, 0, sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(b->work_d, 0, sizeof(unsigned long long) * b->groups.size(), st);
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
     Item &it = b->items[i];
     const mdp_env &env = it.desc.env;
@@ -106,8 +116,11 @@ cudaError_t enqueue(mdp_batch_t *b) {
     if (e == cudaSuccess)
       e = launch_prepare(env.obstacle, env.target, it.m->cls, g.nx, g.ny, g.nt, it.m->delta, it.L, st);
   }
-  if (e == cudaSuccess)
-    e = launch_build_warp_batch(b->items_d, b->prefix_d, b->n, b->work_d, b->cap_bins, b->kmax, 0, st);
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    const auto &G = b->groups[g];
+    e = launch_build_warp_batch(b->items_d + G.start, b->prefix_d + G.pstart, G.n, b->work_d + g, b->cap_bins,
+                                G.K, G.spw, st);
+  }
   if (e == cudaSuccess) e = launch_build_fp32_batch(b->items_d, b->n, b->cta_smem, b->cta_threads, st);
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
     Item &it = b->items[i];
@@ -116,6 +129,10 @@ cudaError_t enqueue(mdp_batch_t *b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(it.stats, 0, sizeof(double) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(it.desc.V, 0, vbytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(it.Vb, 0, vbytes, st);
+    // sweep 1 recomputes every layer (flags [0][0..nt) = 1, the rest 0)
+    const int nt = it.m->nt;
+    if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags, 1, (size_t)nt, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags + nt, 0, 2 * (size_t)nt + 3, st);
   }
   for (int k = 1; k <= b->max_sweeps_all && e == cudaSuccess; ++k)
     e = launch_bellman_batch(b->sitems_d, b->ctas_d, b->n_ctas, k, b->stage_bytes, st);
@@ -228,6 +245,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     b->cta_threads = it.hook.threads;
     const size_t vbytes = sizeof(float) * (size_t)(m->nS + 1);
     ce = dev_alloc((void **)&it.Vb, vbytes, b->st);
+    if (ce == cudaSuccess) ce = dev_alloc((void **)&it.lflags, 3 * ((size_t)m->nt + 1), b->st);
     if (ce == cudaSuccess) ce = dev_alloc((void **)&it.res, sizeof(unsigned long long) * it.max_sweeps, b->st);
     if (ce == cudaSuccess) ce = dev_alloc((void **)&it.stats, sizeof(double) * 4, b->st);
     if (ce != cudaSuccess) return fail(cuda_fail(ce, "batch allocation"));
@@ -244,6 +262,9 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     si.a.nS = m->nS; si.a.Nc = m->Nc; si.a.n_slices = m->n_slices;
     si.a.A = m->A; si.a.A_pad = m->A_pad; si.a.spw = m->spw; si.a.N = m->N; si.a.nbins = m->nbins;
     si.a.tol = tol;
+    si.a.nt = m->nt;
+    si.a.lflags = it.lflags;
+    si.a.work = nullptr;
     si.Va = static_cast<float *>(it.desc.V);
     si.Vb = it.Vb;
     si.policy = it.desc.policy;
@@ -254,15 +275,42 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
       ctas.push_back({i, lo, std::min<int64_t>(m->n_slices, lo + per_cta)});
   }
   b->n_ctas = (int)ctas.size();
+  // group the build items by (states per warp, mode count); prefix segments per group
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  auto cls = [&](int i) {
+    const int sc = args[i].spw == 1 ? 0 : (args[i].spw == 2 ? 1 : 2);
+    return sc * 64 + std::min<int>(args[i].K, 63);
+  };
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cls(x) < cls(y); });
+  std::vector<BuildArgs> sorted(n);
+  std::vector<int64_t> gprefix;
+  for (int j = 0; j < n;) {
+    int e = j;
+    while (e < n && cls(ord[e]) == cls(ord[j])) ++e;
+    mdp_batch_t::Group G{j, e - j, (int)gprefix.size(), args[ord[j]].K, args[ord[j]].spw};
+    if (G.spw != 1 && G.spw != 2) G.spw = 0;
+    int64_t acc = 0;
+    gprefix.push_back(0);
+    for (int q = j; q < e; ++q) {
+      sorted[q] = args[ord[q]];
+      acc += args[ord[q]].n_slices;
+      gprefix.push_back(acc);
+    }
+    b->groups.push_back(G);
+    j = e;
+  }
+  (void)prefix;
   ce = dev_alloc((void **)&b->items_d, sizeof(BuildArgs) * n, b->st);
-  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->prefix_d, sizeof(int64_t) * (n + 1), b->st);
-  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->work_d, sizeof(unsigned long long), b->st);
+  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->prefix_d, sizeof(int64_t) * gprefix.size(), b->st);
+  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->work_d, sizeof(unsigned long long) * b->groups.size(), b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->sitems_d, sizeof(BatchSolveItem) * n, b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->ctas_d, sizeof(BatchCta) * ctas.size(), b->st);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(b->items_d, args.data(), sizeof(BuildArgs) * n, cudaMemcpyHostToDevice, b->st);
+    ce = cudaMemcpyAsync(b->items_d, sorted.data(), sizeof(BuildArgs) * n, cudaMemcpyHostToDevice, b->st);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(b->prefix_d, prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->st);
+    ce = cudaMemcpyAsync(b->prefix_d, gprefix.data(), sizeof(int64_t) * gprefix.size(), cudaMemcpyHostToDevice,
+                         b->st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(b->sitems_d, sitems.data(), sizeof(BatchSolveItem) * n, cudaMemcpyHostToDevice, b->st);
   if (ce == cudaSuccess)

@@ -364,15 +364,16 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
 
 // Active-layer Jacobi sweep k: layer t needs recomputing if its own values
 // or those of layer t+1 changed in sweep k-1 (otherwise V_{k+1} = V_k on it
-// and the output table already holds that value from sweep k-1).  Narrows
+// and the output table already holds that value from sweep k-1).  Sets
 // [sl_lo, sl_hi) to the slices of the first through the last such layer
 // (layers in between are recomputed, which yields their unchanged values).
-// CTA 0 clears the flags that sweep k+1 will set.  Returns false when no
-// layer changed: V_{k+1} = V_k, the residual stays 0.  All threads call it.
-__device__ __forceinline__ bool active_range(const SolveArgs &a, int k, PipeRange &pr) {
+// The leader CTA (one per model) clears the flags that sweep k+1 will set.
+// Returns false when no layer changed: V_{k+1} = V_k, the residual stays 0.
+// All threads of the CTA call it.
+__device__ __forceinline__ bool active_range(const SolveArgs &a, int k, PipeRange &pr, bool leader) {
   const int nt = a.nt;
   const uint8_t *prev = a.lflags + (size_t)((k - 1) % 3) * (nt + 1);
-  if (blockIdx.x == 0) {
+  if (leader) {
     uint8_t *clr = a.lflags + (size_t)((k + 1) % 3) * (nt + 1);
     for (int t = threadIdx.x; t <= nt; t += blockDim.x) clr[t] = 0;
   }
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, VS
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double wmax[kWarps * NO];
   __shared__ int wst_s[kWarps * kDepth];   // columns of the slice in each stage
-  if (a.lflags && k >= 1 && !active_range(a, k, pr)) return;
+  if (a.lflags && k >= 1 && !active_range(a, k, pr, blockIdx.x == 0)) return;
   const int64_t total = pr.sl_hi - pr.sl_lo;
   const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
   const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
@@ -428,13 +429,22 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   pr.s_hi = it.a.nS;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
+  // active-layer sweeps: this CTA's slices intersected with the model's
+  // recomputed range (the model's first CTA clears its next flags)
+  if (it.a.lflags) {
+    PipeRange act = pr;
+    if (!active_range(it.a, k, act, c.sl_lo == 0)) return;
+    pr.sl_lo = max(c.sl_lo, act.sl_lo);
+    pr.sl_hi = min(c.sl_hi, act.sl_hi);
+    if (pr.sl_lo >= pr.sl_hi) return;
+  }
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
   v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
   v.out = reinterpret_cast<VPack<float, 1> *>((k & 1) ? it.Vb : it.Va);
   v.pol[0] = it.policy;
   v.res[0] = it.res;
-  bellman_body<float, 1>(it.a, v, k, c.sl_lo, c.sl_hi, pr, sm, wmax, wst_s);
+  bellman_body<float, 1>(it.a, v, k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
 }
 
 // Per model (one block each): sweeps and residual, final iterate into Va.

@@ -61,12 +61,23 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
                                              float vby, int K, float lam) {
   float wx = vbx, wy = vby;
   if constexpr (KT < 0) {
+    if ((K & 1) == 0) {   // even K: rows are 8-byte aligned (coeffs 16-byte aligned)
 #pragma unroll
-    for (int k = 0; k < -KT; ++k) {
-      if (k < K) {
-        const float yk = __ldg(yw + k);
-        wx = fmaf(yk, phx[k], wx);
-        wy = fmaf(yk, phy[k], wy);
+      for (int k = 0; k < -KT; k += 2) {
+        if (k < K) {
+          const float2 v = __ldg(reinterpret_cast<const float2 *>(yw + k));
+          wx = fmaf(v.x, phx[k], wx); wy = fmaf(v.x, phy[k], wy);
+          wx = fmaf(v.y, phx[k + 1], wx); wy = fmaf(v.y, phy[k + 1], wy);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < -KT; ++k) {
+        if (k < K) {
+          const float yk = __ldg(yw + k);
+          wx = fmaf(yk, phx[k], wx);
+          wy = fmaf(yk, phy[k], wy);
+        }
       }
     }
   } else if constexpr (KT > 0 && (KT % 4) == 0) {
@@ -200,10 +211,16 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   // item role: state q_t, realizations wi, wi + 32/spw, ...
   const int q_t = lane % spw, wi = lane / spw, wstep = 32 / spw;
   const float lam = a.lam;
+  // model scalars in registers: the loops below also store to memory, so
+  // loads through `a` (global memory in the batched kernel) would repeat
+  const int N = a.N, nx = a.nx, ny = a.ny;
+  const int64_t Nc = a.Nc;
+  const uint8_t *__restrict__ cls = a.cls;
+  const float *__restrict__ gbar = static_cast<const float *>(a.gbar);
   const float *Yall = static_cast<const float *>(a.Y);
   const float *vbar = static_cast<const float *>(a.vbar);
   const float *modes = static_cast<const float *>(a.modes);
-  const float invN = 1.0f / (float)a.N;
+  const float invN = 1.0f / (float)N;
   const RankTab rx = rank_tab(a, tab, 0), ry = rank_tab(a, tab, 1);   // (load_rank_tables)
   const int Sx = a.act.Dx + 1, Sy = a.act.Dy + 1;
 
@@ -222,7 +239,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     float vbx = 0.f, vby = 0.f;
     const float *Yt = Yall;
     if (kind_t == KIND_SAMPLE) {
-      const int64_t t = s_t / a.Nc, c = s_t % a.Nc;
+      const int64_t t = s_t / Nc, c = s_t % Nc;
       vbx = vbar[2 * s_t];
       vby = vbar[2 * s_t + 1];
 #pragma unroll
@@ -233,16 +250,16 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
           phy[k] = 0.f;
           continue;
         }
-        const float2 ph = *reinterpret_cast<const float2 *>(modes + 2 * ((t * K + k) * a.Nc + c));
+        const float2 ph = *reinterpret_cast<const float2 *>(modes + 2 * ((t * K + k) * Nc + c));
         phx[k] = ph.x;
         phy[k] = ph.y;
       }
-      Yt = Yall + (size_t)t * a.N * K;
+      Yt = Yall + (size_t)t * N * K;
     }
     // ---- pass 1: exact extremes of u per state
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
     if (kind_t == KIND_SAMPLE) {
-      for (int w = wi; w < a.N; w += wstep) {
+      for (int w = wi; w < N; w += wstep) {
         const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
         mnx = fminf(mnx, u.x); mxx = fmaxf(mxx, u.x);
         mny = fminf(mny, u.y); mxy = fmaxf(mxy, u.y);
@@ -308,7 +325,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     if (kind_t == KIND_SAMPLE) {
       const uint32_t gbase = smem_u32(grid + gt.base);
 #pragma unroll 1
-      for (int w = wi; w < a.N; w += wstep) {
+      for (int w = wi; w < N; w += wstep) {
         const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
         int X = fine_coord(u.x, gt.n0x, Sx, rx) - gt.xmin;
         int Y = fine_coord(u.y, gt.n0y, Sy, ry) - gt.ymin;
@@ -359,9 +376,9 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   const int64_t ir = sl * 32 + lane;
   int e = 0;
   uint32_t sink = 0;
-  const int64_t t = s_l / a.Nc, c = s_l % a.Nc;
-  const int ci = (int)(c % a.nx), cj = (int)(c / a.nx);
-  const int64_t nxt = (t + 1) * a.Nc;
+  const int64_t t = s_l / Nc, c = s_l % Nc;
+  const int ci = (int)(c % nx), cj = (int)(c / nx);
+  const int64_t nxt = (t + 1) * Nc;
   if (kind_l == KIND_SAMPLE && active) {
     for (int dj = loy; dj <= hiy; ++dj) {
       const int jp = cj + dj;
@@ -369,14 +386,14 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
         const uint32_t n = bin_count(di, dj);
         if (n == 0) continue;
         const int ip = ci + di;
-        const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
-        const uint8_t cc = inside ? a.cls[nxt + (int64_t)jp * a.nx + ip] : CLS_OBSTACLE;
+        const bool inside = ip >= 0 && ip < nx && jp >= 0 && jp < ny;
+        const uint8_t cc = inside ? cls[nxt + (int64_t)jp * nx + ip] : CLS_OBSTACLE;
         if (cc & CLS_OBSTACLE) sink += n;
         else ++e;
       }
     }
   } else if (kind_l == KIND_SINK) {
-    sink = (uint32_t)a.N;
+    sink = (uint32_t)N;
   }
   const bool cap_hit = e + (sink > 0 ? 1 : 0) > a.row_cap;
   if (cap_hit) {
@@ -397,20 +414,20 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   int k = 0;
   if (kind_l == KIND_SAMPLE && active) {
     const float F = a.act.F[a_l];
-    const float g_s = a.gbar ? static_cast<const float *>(a.gbar)[s_l] : 0.f;
+    const float g_s = gbar ? gbar[s_l] : 0.f;
     for (int dj = loy; dj <= hiy; ++dj) {
       const int jp = cj + dj;
       for (int di = lox; di <= hix; ++di) {
         const uint32_t n = bin_count(di, dj);
         if (n == 0) continue;
         const int ip = ci + di;
-        const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
-        const uint8_t cc = inside ? a.cls[nxt + (int64_t)jp * a.nx + ip] : CLS_OBSTACLE;
+        const bool inside = ip >= 0 && ip < nx && jp >= 0 && jp < ny;
+        const uint8_t cc = inside ? cls[nxt + (int64_t)jp * nx + ip] : CLS_OBSTACLE;
         if (cc & CLS_OBSTACLE) continue;
-        if (write) dst[(size_t)k * 32] = entry_word(dj * a.nx + di, n);
+        if (write) dst[(size_t)k * 32] = entry_word(dj * nx + di, n);
         ++k;
         const bool is_t = (cc & CLS_TARGET) != 0;
-        const float g_sp = a.gbar ? static_cast<const float *>(a.gbar)[nxt + (int64_t)jp * a.nx + ip] : 0.f;
+        const float g_sp = gbar ? gbar[nxt + (int64_t)jp * nx + ip] : 0.f;
         const float p = (float)n * invN;
         for (int o = 0; o < a.rw.n_obj; ++o)
           Racc[o] = fmaf(p, step_reward32(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t), Racc[o]);
@@ -447,7 +464,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   if (lane == 0) {
     acc.nnz += (unsigned long long)tot;
     acc.dom += (unsigned long long)dom;
-    acc.samples += (unsigned long long)sampled * (unsigned long long)a.N;
+    acc.samples += (unsigned long long)sampled * (unsigned long long)N;
     if ((unsigned long long)W > acc.maxrow) acc.maxrow = W;
   }
 }

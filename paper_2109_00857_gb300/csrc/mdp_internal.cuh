@@ -215,11 +215,12 @@ cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm);
 cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, const BatchCta *ctas_d, int n_ctas, int k,
                                  int stage_bytes, cudaStream_t st);
 cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st);
-// batched build (FP32): one persistent warp launch over every model's slices
-// (prefix[m] = first global slice of model m, prefix[n] = total), then the
+// batched build (FP32): one persistent warp launch over the slices of n
+// models that share the mode count K and the states per warp spw (prefix[m]
+// = first slice of model m in the launch, prefix[n] = total); then the
 // full-window CTA kernel over every model's deferred slices
 cudaError_t launch_build_warp_batch(const BuildArgs *items_d, const int64_t *prefix_d, int n,
-                                    unsigned long long *work_d, int cap_bins, int kmax, int spw_all,
+                                    unsigned long long *work_d, int cap_bins, int K, int spw,
                                     cudaStream_t st);
 cudaError_t launch_build_fp32_batch(const BuildArgs *items_d, int n, size_t smem, int threads,
                                     cudaStream_t st);
