@@ -245,12 +245,15 @@ mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const double *sig
                              void *stream);
 
 /* ------------------------------------------------------------- batching --
- * Builds and solves n independent MDPs (uneven sizes) with one persistent
- * build launch over a shared work queue and one batched Bellman launch per
- * sweep, all captured in a CUDA graph that is replayed on each call with the
- * same shapes.  Arrays are host arrays of per-MDP descriptors; V[i] / policy[i]
- * are device outputs as in mdp_solve (FP32 only).  Objective slot 0 of each
- * MDP is solved with Jacobi to tol. */
+ * Builds and solves n (1..1023) independent MDPs of uneven sizes: one
+ * persistent build launch per group of MDPs with the same mode count and
+ * action count class over a shared work queue, and per Jacobi sweep one
+ * small plan launch plus one Bellman launch that spreads every MDP's
+ * recomputed layers evenly over the GPU; all captured in a CUDA graph that is
+ * replayed on each call with the same shapes.  Arrays are host arrays of
+ * per-MDP descriptors; V[i] / policy[i] are device outputs as in mdp_solve
+ * (FP32 only).  Objective slot 0 of each MDP is solved with (active-layer)
+ * Jacobi to tol; results equal mdp_build + mdp_solve of each MDP alone. */
 typedef struct {
   mdp_env env;
   mdp_grid grid;

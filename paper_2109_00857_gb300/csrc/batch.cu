@@ -12,9 +12,10 @@
 // Run: one persistent warp-per-slice launch per states-per-warp class
 // builds its items' slices from one work queue; one CTA launch finishes the
 // slices any item deferred;
-// each Jacobi sweep is one launch over all items (CTAs own contiguous slice
-// ranges of one item, narrowed in-kernel to the layers whose inputs changed
-// in the previous sweep; an item stops on its own residual); one launch
+// each Jacobi sweep is a one-block plan launch that cuts every item's
+// recomputed layers (those whose inputs changed in the previous sweep) into
+// chunks of equal size, and one launch whose CTAs take one chunk each (an
+// item stops on its own residual); one launch
 // finalizes all.  The whole sequence (with the per-item coefficient draws,
 // cell classes, clears and the status copies) is captured once into a CUDA
 // graph and replayed on every run.
@@ -135,7 +136,7 @@ cudaError_t enqueue(mdp_batch_t *b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags + nt, 0, 2 * (size_t)nt + 3, st);
   }
   for (int k = 1; k <= b->max_sweeps_all && e == cudaSuccess; ++k)
-    e = launch_bellman_batch(b->sitems_d, b->ctas_d, b->n_ctas, k, b->stage_bytes, st);
+    e = launch_bellman_batch(b->sitems_d, b->n, b->ctas_d, b->n_ctas, k, b->stage_bytes, st);
   if (e == cudaSuccess) e = launch_finalize_batch(b->sitems_d, b->n, st);
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
     Item &it = b->items[i];
@@ -155,8 +156,8 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     return MDP_ERR_ARG;
   }
   *out = nullptr;
-  if (!items_h || n < 1 || n > 4096) {
-    set_error("invalid argument: need 1 <= n <= 4096 items");
+  if (!items_h || n < 1 || n > 1023) {
+    set_error("invalid argument: need 1 <= n <= 1023 items");
     return MDP_ERR_ARG;
   }
   int ndev = 0;
@@ -220,12 +221,10 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   std::vector<BuildArgs> args(n);
   std::vector<int64_t> prefix(n + 1, 0);
   std::vector<BatchSolveItem> sitems(n);
-  std::vector<BatchCta> ctas;
+
   int per_sm = 1;
   cudaError_t ce = prepare_bellman_batch(wcap, &b->stage_bytes, &per_sm);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "prepare_bellman_batch"));
-  const int64_t cta_target = (int64_t)num_sms() * std::max(per_sm, 1) * 4;   // ~4 waves
-  const int64_t per_cta = std::max<int64_t>(32, (total_slices + cta_target - 1) / cta_target);
   for (int i = 0; i < n; ++i) {
     Item &it = b->items[i];
     mdp_build_opts o{};
@@ -271,10 +270,10 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     si.res = it.res;
     si.stats = it.stats;
     si.max_sweeps = it.max_sweeps;
-    for (int64_t lo = 0; lo < m->n_slices; lo += per_cta)
-      ctas.push_back({i, lo, std::min<int64_t>(m->n_slices, lo + per_cta)});
   }
-  b->n_ctas = (int)ctas.size();
+  // sweep grid: two waves of CTAs share each sweep's recomputed slices (plus
+  // one entry per model for the chunk remainders)
+  b->n_ctas = num_sms() * std::max(per_sm, 1) * 2;
   // group the build items by (states per warp, mode count); prefix segments per group
   std::vector<int> ord(n);
   for (int i = 0; i < n; ++i) ord[i] = i;
@@ -305,7 +304,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->prefix_d, sizeof(int64_t) * gprefix.size(), b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->work_d, sizeof(unsigned long long) * b->groups.size(), b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->sitems_d, sizeof(BatchSolveItem) * n, b->st);
-  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->ctas_d, sizeof(BatchCta) * ctas.size(), b->st);
+  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->ctas_d, sizeof(BatchCta) * (b->n_ctas + n), b->st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(b->items_d, sorted.data(), sizeof(BuildArgs) * n, cudaMemcpyHostToDevice, b->st);
   if (ce == cudaSuccess)
@@ -313,8 +312,6 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
                          b->st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(b->sitems_d, sitems.data(), sizeof(BatchSolveItem) * n, cudaMemcpyHostToDevice, b->st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(b->ctas_d, ctas.data(), sizeof(BatchCta) * ctas.size(), cudaMemcpyHostToDevice, b->st);
   if (ce == cudaSuccess) ce = cudaMallocHost((void **)&b->cnt_h, sizeof(unsigned long long) * CNT_N * n);
   if (ce == cudaSuccess) ce = cudaMallocHost((void **)&b->stats_h, sizeof(double) * 4 * n);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->st);

@@ -411,8 +411,75 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, VS
   bellman_body<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
 }
 
+// Plan of batched Jacobi sweep k (one block): per model, the slices of the
+// layers whose inputs changed in sweep k-1 (nothing once the model met the
+// tolerance or ran max_sweeps), with the model's flags for sweep k+1
+// cleared; then the total is cut into chunks of about total / G slices,
+// each model's range into whole chunks, so every CTA entry of the sweep
+// holds one model's contiguous range (entries past the last: item -1).
+// n <= blockDim.x.
+__global__ void plan_batch_kernel(const BatchSolveItem *items, int n, int k, BatchCta *ctas, int G,
+                                  int n_entries) {
+  __shared__ long long s_cnt[1024];
+  __shared__ int s_ctas[1024];
+  __shared__ long long s_chunk;
+  const int i = threadIdx.x;
+  long long lo = 0, hi = 0;
+  if (i < n) {
+    const BatchSolveItem &it = items[i];
+    const SolveArgs &a = it.a;
+    const bool done = k > it.max_sweeps ||
+                      (k > 1 && __longlong_as_double((long long)it.res[k - 2]) <= a.tol) ||
+                      *(volatile int *)a.err;
+    if (a.lflags) {
+      const int nt = a.nt;
+      const uint8_t *prev = a.lflags + (size_t)((k - 1) % 3) * (nt + 1);
+      uint8_t *clr = a.lflags + (size_t)((k + 1) % 3) * (nt + 1);
+      int tlo = nt, thi = -1;
+      for (int t = 0; t < nt; ++t) {
+        if (prev[t] | prev[t + 1]) {
+          tlo = min(tlo, t);
+          thi = t;
+        }
+      }
+      for (int t = 0; t <= nt; ++t) clr[t] = 0;
+      if (thi >= 0 && !done) {
+        lo = (long long)tlo * a.Nc / a.spw;
+        hi = min((long long)a.n_slices, ((long long)(thi + 1) * a.Nc + a.spw - 1) / a.spw);
+      }
+    } else if (!done) {
+      hi = a.n_slices;
+    }
+  }
+  s_cnt[i] = hi - lo;
+  __syncthreads();
+  if (i == 0) {
+    long long tot = 0;
+    for (int j = 0; j < n; ++j) tot += s_cnt[j];
+    s_chunk = max(32LL, (tot + G - 1) / G);
+  }
+  __syncthreads();
+  const long long chunk = s_chunk;
+  s_ctas[i] = (i < n) ? (int)((s_cnt[i] + chunk - 1) / chunk) : 0;
+  __syncthreads();
+  if (i < n) {
+    int first = 0;
+    for (int j = 0; j < i; ++j) first += s_ctas[j];
+    for (int c = 0; c < s_ctas[i] && first + c < n_entries; ++c) {
+      const long long a0 = lo + (long long)c * chunk;
+      ctas[first + c] = BatchCta{i, a0, min(hi, a0 + chunk)};
+    }
+  }
+  if (i == n) {   // unused entries
+    int used = 0;
+    for (int j = 0; j < n; ++j) used += s_ctas[j];
+    for (int e = used; e < n_entries; ++e) ctas[e] = BatchCta{-1, 0, 0};
+  }
+}
+
 // Batched Jacobi sweep k over many models: CTA b works on ctas[b] (one
-// model's contiguous slice range); each model stops on its own residual.
+// model's contiguous slice range, from the plan); each model stops on its
+// own residual.
 __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const BatchSolveItem *items,
                                                                     const BatchCta *ctas, int k,
                                                                     int stage_bytes) {
@@ -420,8 +487,8 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   __shared__ double wmax[kWarps];
   __shared__ int wst_s[kWarps * kDepth];
   const BatchCta c = ctas[blockIdx.x];
+  if (c.item < 0) return;
   const BatchSolveItem &it = items[c.item];
-  if (k > it.max_sweeps) return;
   PipeRange pr;
   pr.sl_lo = c.sl_lo;
   pr.sl_hi = c.sl_hi;
@@ -429,15 +496,6 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   pr.s_hi = it.a.nS;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
-  // active-layer sweeps: this CTA's slices intersected with the model's
-  // recomputed range (the model's first CTA clears its next flags)
-  if (it.a.lflags) {
-    PipeRange act = pr;
-    if (!active_range(it.a, k, act, c.sl_lo == 0)) return;
-    pr.sl_lo = max(c.sl_lo, act.sl_lo);
-    pr.sl_hi = min(c.sl_hi, act.sl_hi);
-    if (pr.sl_lo >= pr.sl_hi) return;
-  }
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
   v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
@@ -464,10 +522,14 @@ __global__ void finalize_batch_kernel(const BatchSolveItem *items) {
   for (int64_t i = threadIdx.x; i <= it.a.nS; i += blockDim.x) it.Va[i] = it.Vb[i];
 }
 
-cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, const BatchCta *ctas_d, int n_ctas, int k,
+cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
                                  int stage_bytes, cudaStream_t st) {
+  if (n > 1023) return cudaErrorInvalidValue;
+  plan_batch_kernel<<<1, 1024, 0, st>>>(items_d, n, k, ctas_d, G, G + n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const size_t smem = 256 + (size_t)kWarps * kDepth * stage_bytes;
-  bellman_batch_kernel<<<n_ctas, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+  bellman_batch_kernel<<<G + n, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
   return cudaGetLastError();
 }
 

@@ -212,7 +212,9 @@ struct BatchCta {
   int64_t sl_lo, sl_hi;
 };
 cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm);
-cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, const BatchCta *ctas_d, int n_ctas, int k,
+// sweep k: a plan launch spreads the models' recomputed slices over G + n
+// CTA entries (ctas_d), then the sweep launch; n <= 1023 models
+cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
                                  int stage_bytes, cudaStream_t st);
 cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st);
 // batched build (FP32): one persistent warp launch over the slices of n

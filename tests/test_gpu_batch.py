@@ -47,6 +47,25 @@ def test_batch_equals_members_alone_and_replays(mdp):
     b.close()
 
 
+def test_batch_with_tolerance_stops_each_member_on_its_own(mdp):
+    # members converge at different sweeps; the per-sweep plan must drop each
+    # one as soon as its own residual meets tol and still match the solo solve
+    envs = members()[:6]
+    denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
+    for tol in (1e-3, 0.5):
+        b = mdp.Batch(denvs, tol=tol)
+        sweeps, ms = b.run()
+        solo = []
+        for i, (e, d) in enumerate(zip(envs, denvs)):
+            m = mdp.mdp_build(d, objs=(e.objectives[0],))
+            V, pi, st = mdp.mdp_solve(m, 0, tol=tol)
+            solo.append(st.sweeps)
+            assert sweeps[i] == st.sweeps, (tol, i, sweeps[i], st.sweeps)
+            assert np.array_equal(b.V[i].cpu().numpy(), V.cpu().numpy()), (tol, i)
+            assert np.array_equal(b.policy[i].cpu().numpy(), pi.cpu().numpy()), (tol, i)
+        b.close()
+
+
 def test_batch_rejects_fp64_items(mdp):
     e = inputs.tiny()
     with pytest.raises(mdp.MdpError):
