@@ -335,7 +335,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-rates", default="20,50,100,200")
+    ap.add_argument("--serve-rates", default="20,50,100,200,400,800")
     ap.add_argument("--solve", default="jacobi", choices=["jacobi", "jacobi_full", "layered"])
     ap.add_argument("--separate", action="store_true",
                     help="solve the objectives one after another instead of one fused solve")

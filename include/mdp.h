@@ -287,14 +287,16 @@ typedef struct {
   uint64_t seed;
   int32_t N;
   int32_t objective;             /* mdp_objective */
-  double tol;
+  double tol;                    /* 0: the exact fixed point by one layered pass (the
+                                    Jacobi fixed point bit for bit); > 0: Jacobi sweeps
+                                    until the residual is <= tol */
 } mdp_request;
 
 typedef struct {
   int32_t status;                /* mdp_status of the request */
   float V_start;                 /* V at (t = 0, start) */
   int16_t pi_start;              /* policy at (t = 0, start) */
-  int32_t sweeps;
+  int32_t sweeps;                /* Jacobi sweeps (1 for the layered pass) */
   double latency_ms;             /* submit -> completion (host clock) */
   double queue_ms;               /* submit -> admission */
   int64_t device_bytes;          /* memory the request held */
