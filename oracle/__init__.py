@@ -82,6 +82,8 @@ def lib():
                                           P, P, P]
             l.orc_vi_backward.restype = C.c_int
             l.orc_q_values.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P, P]
+            l.orc_rollout.argtypes = [C.POINTER(Problem), P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P, P]
+            l.orc_rollout.restype = C.c_int
             _lib = l
     return _lib
 
@@ -273,3 +275,25 @@ def model_from_csr(nS, A, N, rowptr, col, cnt, R=None) -> OracleModel:
                     np.ascontiguousarray(col, dtype=np.int64),
                     np.ascontiguousarray(cnt, dtype=np.int32), N, R, None, 0)
     return m
+
+
+# ----------------------------------------------------------------- rollouts --
+def rollout(env, policy, start, objs=(OBJ_TIME,), with_traj=False):
+    """Policy rollouts from start = (i0, j0) at t = 0 over the env's N
+    realizations (Sec. IV).  policy: [nS] (-1 where undefined).  Returns
+    (ret [N][n_obj], steps [N], status [N] (0 target, 1 sink), traj
+    [N][nt+1] state after k steps (sink = nS, -1 after the end) or None)."""
+    keep = []
+    p = make_problem(env, keep)
+    pol = np.ascontiguousarray(policy, dtype=np.int32)
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    N = env.N
+    ret = np.zeros((N, len(ob)), dtype=np.float64)
+    steps = np.zeros(N, dtype=np.int32)
+    status = np.zeros(N, dtype=np.int32)
+    traj = np.zeros((N, env.nt + 1), dtype=np.int64) if with_traj else None
+    st = lib().orc_rollout(C.byref(p), _p(pol), int(start[0]), int(start[1]), _p(ob), len(ob), _p(ret),
+                           _p(steps), _p(status), _p(traj))
+    if st != 0:
+        raise ValueError(f"oracle rollout rejected its arguments ({st})")
+    return ret, steps, status, traj

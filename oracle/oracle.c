@@ -337,3 +337,69 @@ int orc_vi_backward(int64_t nS, int32_t A, int32_t nt, int64_t Nc, const int64_t
     }
   return 0;
 }
+
+/* -------------------------------------------------------------- rollouts -- */
+int orc_rollout(const orc_problem *p, const int32_t *policy, int32_t i0, int32_t j0,
+                const int32_t *objs, int32_t n_obj, double *ret, int32_t *steps, int32_t *status,
+                int64_t *traj) {
+  if (n_obj < 1 || n_obj > 3 || p->N < 1 || p->nt < 1) return -2;
+  if (i0 < 0 || i0 >= p->nx || j0 < 0 || j0 >= p->ny) return -2;
+  for (int32_t o = 0; o < n_obj; ++o)
+    if (objs[o] < 0 || objs[o] > 2 || (objs[o] == ORC_OBJ_NET_ENERGY && p->gbar == NULL)) return -2;
+  const int64_t Nx = p->nx, Ny = p->ny, Nt = p->nt, Nc = Nx * Ny, nS = Nt * Nc;
+  const int32_t K = p->K, N = p->N;
+  for (int32_t w = 0; w < N; ++w) {
+    double *rw = ret + (int64_t)w * n_obj;
+    int64_t *tr = traj ? traj + (int64_t)w * (Nt + 1) : NULL;
+    for (int32_t o = 0; o < n_obj; ++o) rw[o] = 0.0;
+    if (tr)
+      for (int64_t k = 0; k <= Nt; ++k) tr[k] = -1;
+    int64_t i = i0, j = j0;
+    int32_t n = 0, st = 1;
+    if (tr) tr[0] = j * Nx + i;
+    for (int64_t t = 0; t < Nt; ++t) {
+      const int64_t c = j * Nx + i, s = t * Nc + c;
+      if (p->target[c]) { /* arrived: terminal states are absorbing */
+        st = 0;
+        break;
+      }
+      const int32_t a = policy[s];
+      if (p->obstacle[s] || t == Nt - 1 || a < 0) { /* every move ends in the sink */
+        for (int32_t o = 0; o < n_obj; ++o) rw[o] = rw[o] + p->r_outbound;
+        ++n;
+        if (tr) tr[n] = nS;
+        st = 1;
+        break;
+      }
+      const double dxa = p->act[3 * a + 0], dya = p->act[3 * a + 1], F = p->act[3 * a + 2];
+      /* realization w's velocity at this state and time: vbar + sum_k Y_k v~_k */
+      double vx = p->vbar[2 * s + 0], vy = p->vbar[2 * s + 1];
+      const double *yw = p->Y + (t * N + w) * K;
+      for (int32_t k = 0; k < K; ++k) {
+        const double *phi = p->modes + 2 * ((t * K + k) * Nc + c);
+        vx = vx + yw[k] * phi[0];
+        vy = vy + yw[k] * phi[1];
+      }
+      const double x = ((double)i + 0.5) * p->dx, y = ((double)j + 0.5) * p->dx;
+      const double xp = x + (vx + dxa) * p->dt, yp = y + (vy + dya) * p->dt;
+      const int64_t ip = (int64_t)floor(xp / p->dx), jp = (int64_t)floor(yp / p->dx);
+      ++n;
+      if (ip < 0 || ip >= Nx || jp < 0 || jp >= Ny || p->obstacle[(t + 1) * Nc + jp * Nx + ip]) {
+        for (int32_t o = 0; o < n_obj; ++o) rw[o] = rw[o] + p->r_outbound;
+        if (tr) tr[n] = nS;
+        st = 1;
+        break;
+      }
+      const int is_t = p->target[jp * Nx + ip] != 0;
+      const double g_s = p->gbar ? p->gbar[s] : 0.0;
+      const double g_sp = p->gbar ? p->gbar[(t + 1) * Nc + jp * Nx + ip] : 0.0;
+      for (int32_t o = 0; o < n_obj; ++o) rw[o] = rw[o] + step_reward(p, objs[o], F, g_s, g_sp, is_t);
+      i = ip;
+      j = jp;
+      if (tr) tr[n] = (t + 1) * Nc + jp * Nx + ip;
+    }
+    steps[w] = n;
+    status[w] = st;
+  }
+  return 0;
+}

@@ -96,6 +96,23 @@ int orc_vi_backward(int64_t nS, int32_t A, int32_t nt, int64_t Nc, const int64_t
 void orc_q_values(int64_t nS, int32_t A, const int64_t *rowptr, const int64_t *col,
                   const double *prob, const double *R, const double *V, double *Q);
 
+/* Policy rollouts (Sec. IV: the optimal policy applied to every flow
+ * realization from the start).  Path w starts at cell (i0, j0) at t = 0 and
+ * follows policy[s] (s = t*Nc + j*Nx + i), moving with realization w's
+ * velocity of time t at its state (the build's kinematics), until:
+ *   status 0  it stands on a target cell (absorbing, no further reward);
+ *   status 1  it takes the sink: a landing outside the domain or on an
+ *             obstacle at t+1, any move from the last layer t = Nt-1, or a
+ *             state whose policy is -1 (an obstacle start); reward r_outbound.
+ * Each step adds the one-step reward of objective objs[o] (target landings
+ * add r_term), summed in path order.
+ * Outputs: ret[w*n_obj + o], steps[w], status[w]; traj[w*(nt+1) + k] = state
+ * after k steps (k = 0: the start; the sink = |S|; -1 after the end), or
+ * NULL.  Returns 0, or -2 on bad arguments. */
+int orc_rollout(const orc_problem *p, const int32_t *policy, int32_t i0, int32_t j0,
+                const int32_t *objs, int32_t n_obj, double *ret, int32_t *steps, int32_t *status,
+                int64_t *traj);
+
 #ifdef __cplusplus
 }
 #endif
