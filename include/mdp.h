@@ -244,6 +244,34 @@ mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const double *sig
                              uint64_t seed, uint64_t mdp_id, int32_t precision, void *Y,
                              void *stream);
 
+/* ------------------------------------------------------------- rollouts --
+ * Policy rollouts (Sec. IV: the optimal policy applied to every flow
+ * realization from the start; the mean returns are the expected mission
+ * time, energy and net energy).  Path (q, w) starts at cell starts_h[2q],
+ * starts_h[2q+1] at t = 0 and follows policy[s] (device int16 [nt*ny*nx], as
+ * written by mdp_solve), moving with realization w's velocity of time t at
+ * its state -- the build's kinematics with the same env, grid, actions and N
+ * (coefficients from env->coeffs or drawn as mdp_build draws them), so each
+ * move is one of the samples the build counted.  A path ends on a target cell
+ * (status 0) or in the sink (status 1: outside the domain, an obstacle at
+ * t+1, a move from the last layer, or policy -1), which pays r_outbound; each
+ * step adds the one-step reward of objective objs_h[o].
+ * Outputs (each may be NULL): ret device [n_starts][N][n_obj] float (FP32) or
+ * double (FP64_CHECK), steps device int32 [n_starts][N], status device int8
+ * [n_starts][N]; summary_h host [n_starts].  Synchronises `stream` once.
+ * Errors: MDP_ERR_ARG for bad sizes, pointers, objectives or start cells. */
+typedef struct {
+  double mean_return[3];     /* per objective slot, over the N paths */
+  double p_target;           /* fraction of paths that reached a target cell */
+  double mean_steps_target;  /* mean steps of those paths (0 if none) */
+  int64_t paths;             /* N */
+} mdp_rollout_summary;
+
+mdp_status mdp_rollout(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
+                       int32_t N, const int16_t *policy, const int32_t *starts_h, int32_t n_starts,
+                       const int32_t *objs_h, int32_t n_obj, void *ret, int32_t *steps,
+                       int8_t *status, mdp_rollout_summary *summary_h, void *stream);
+
 /* ------------------------------------------------------------- batching --
  * Builds and solves n (1..1023) independent MDPs of uneven sizes: one
  * persistent build launch per group of MDPs with the same mode count and

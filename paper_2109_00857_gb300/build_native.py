@@ -30,6 +30,7 @@ UNITS = {
     "serve.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],
+    "rollout.cu": [],
     "check_fp64.cu": ["-fmad=false"],
 }
 

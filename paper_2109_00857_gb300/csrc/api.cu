@@ -89,7 +89,7 @@ static int pow2_at_least(int x) {
   return p;
 }
 
-static mdp_status check_device() {
+mdp_status check_device() {
   int n = 0;
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess || n == 0) {
@@ -152,7 +152,7 @@ static void offset_thresholds(const float *d, int A, int32_t *c, float *th, floa
   }
 }
 
-static mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out) {
+mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out) {
   if (!ac) return arg_fail("actions is NULL");
   const int A = ac->n_headings * ac->n_speeds;
   if (ac->n_headings < 1 || ac->n_speeds < 1 || A > kMaxActions)

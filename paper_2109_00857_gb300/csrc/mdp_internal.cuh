@@ -157,6 +157,10 @@ mdp_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
 void dev_free(void *p, cudaStream_t st);
 int ensure_device_init();
+// MDP_OK when a CUDA device is usable (sets the error message otherwise)
+mdp_status check_device();
+// validated action table of `ac` (FP32 displacements scaled by lam = dt/dx)
+mdp_status make_actions(const mdp_actions *ac, double lam, ActionTable *t, int *A_out);
 
 // ----------------------------------------------------------- launches ----
 // sampler (FP64 draw; FP32 copy is the FP64 value rounded)

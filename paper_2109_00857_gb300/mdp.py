@@ -64,6 +64,11 @@ class MdpSolveStats(C.Structure):
                 ("backups", C.c_int64)]
 
 
+class MdpRolloutSummary(C.Structure):
+    _fields_ = [("mean_return", C.c_double * 3), ("p_target", C.c_double),
+                ("mean_steps_target", C.c_double), ("paths", C.c_int64)]
+
+
 class MdpBatchItem(C.Structure):
     _fields_ = [("env", MdpEnv), ("grid", MdpGrid), ("actions", MdpActions), ("N", C.c_int32),
                 ("subgrid_L", C.c_int32), ("objective", C.c_int32), ("V", P), ("policy", P)]
@@ -91,6 +96,7 @@ SIGNATURES = {
     "mdp_model_free": (None, [P]),
     "mdp_solve_multi": (C.c_int, [P, C.c_int32, P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_solve_noalloc": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
+    "mdp_rollout": (C.c_int, [P, P, P, C.c_int32, P, P, C.c_int32, P, C.c_int32, P, P, P, P, P]),
     "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
                                     C.c_int32, P, P]),
     "mdp_batch_create": (C.c_int, [P, C.c_int32, C.c_double, P]),
@@ -309,6 +315,30 @@ def mdp_solve_noalloc(model: Model, obj: int = 0, tol: float = 0.0, max_sweeps: 
     _check(load().mdp_solve_noalloc(model.handle, obj, float(tol), int(max_sweeps), _ptr(V),
                                     _ptr(policy), _stream(stream), C.byref(st)), "mdp_solve_noalloc")
     return V, policy, st
+
+
+def mdp_rollout(denv: "DeviceEnv", policy, starts, objs=(MDP_OBJ_TIME,), N: Optional[int] = None,
+                paths: bool = True, stream=None):
+    """Policy rollouts from each start (i, j) at t = 0 over N realizations.
+    Returns (ret [n_starts][N][n_obj], steps [n_starts][N], status [n_starts][N])
+    as torch device tensors (None unless paths) and a list of MdpRolloutSummary."""
+    import torch
+    st = np.ascontiguousarray(starts, dtype=np.int32).reshape(-1, 2)
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    N = denv.env.N if N is None else N
+    n = st.shape[0]
+    ret = steps = status = None
+    if paths:
+        dt = torch.float64 if denv.precision else torch.float32
+        ret = torch.empty((n, N, len(ob)), dtype=dt, device="cuda")
+        steps = torch.empty((n, N), dtype=torch.int32, device="cuda")
+        status = torch.empty((n, N), dtype=torch.int8, device="cuda")
+    e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
+    summ = (MdpRolloutSummary * n)()
+    _check(load().mdp_rollout(C.byref(e), C.byref(g), C.byref(a), int(N), _ptr(policy), st.ctypes.data_as(P), n,
+                              ob.ctypes.data_as(P), len(ob), _ptr(ret), _ptr(steps), _ptr(status), summ,
+                              _stream(stream)), "mdp_rollout")
+    return ret, steps, status, [summ[q] for q in range(n)]
 
 
 def mdp_sample_coeffs(nt: int, N: int, K: int, sigma, seed: int, mdp_id: int = 0,
