@@ -341,6 +341,7 @@ def main():
                     help="solve the objectives one after another instead of one fused solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--threads", type=int, default=0)
@@ -490,6 +491,28 @@ def main():
                       "device_bytes": info.device_bytes}}
     if world > 1:
         line["bellman_updates_per_s"] = backups / (t_ms / 1e3)
+
+    # policy rollouts (Sec. IV) from a grid of starts with the last solve's
+    # time-optimal policy, all N realizations each; outside the timed step
+    if not args.no_rollout:
+        starts = [(i, j) for j in range(env.ny // 16, env.ny, env.ny // 8) for i in range(env.nx // 16, env.nx, env.nx // 8)]
+        n_obj = len(objs)
+        for _ in range(2):
+            rr = mdp.mdp_rollout(denv, Pbuf[0], starts, objs=objs, stream=stream)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        ret_t, steps_t, status_t, summ = mdp.mdp_rollout(denv, Pbuf[0], starts, objs=objs, stream=stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        r_ms = r0.elapsed_time(r1)
+        n_paths = len(starts) * env.N
+        n_steps = int(steps_t.to(torch.int64).sum().item())
+        line["rollout"] = {"starts": len(starts), "paths": n_paths, "steps": n_steps, "ms": r_ms,
+                           "paths_per_s": n_paths / (r_ms / 1e3), "steps_per_s": n_steps / (r_ms / 1e3),
+                           "policy": f"objective {objs[0]}",
+                           "p_target_mean": float(np.mean([q.p_target for q in summ])),
+                           "note": "includes the coefficient draw and the per-start summaries"}
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:
