@@ -136,19 +136,18 @@ struct PipeRange {
   int dtab_smem;          // 1: delta table staged in shared memory
 };
 
-static int stage_bytes_for(int wcap, size_t rsz) {
-  int b = wcap * 128 + 32 * (int)rsz;
-  return (b + 127) & ~127;
-}
+// one stage holds a slice's entry columns (at most wcap of them)
+static int stage_bytes_for(int wcap) { return wcap * 128; }
 
 // A CTA streams a contiguous block of slices (so its V(s') gathers stay in a
 // small window of layer t+1 that L1 keeps); warp w takes slices w, w+8, ...
 // and keeps kDepth of them in flight in private stages: lane 0 copies a
-// slice's entry columns, its 32 R values and its 32 row lengths with
-// cp.async.bulk (TMA) into a stage whose mbarrier counts the bytes, while the
-// warp works on an earlier stage: gathers V(s'), forms Q, reduces max/argmax
-// over each state's A_pad lanes and writes V and the policy.  Slice offsets
-// and widths of the next 32 slices are read in one coalesced load.
+// slice's entry columns with cp.async.bulk (TMA) into a stage whose mbarrier
+// counts the bytes, while the warp works on an earlier stage: gathers V(s'),
+// forms Q, reduces max/argmax over each state's A_pad lanes and writes V and
+// the policy.  The slice's R values (one per row and objective) come with
+// plain coalesced loads issued one slice ahead; slice offsets and widths of
+// the next 32 slices are read in one coalesced load.
 // res != nullptr: Jacobi sweep k (exits at once if sweep k-1 met the
 // tolerance) with the residual reduced into res[k-1].
 // One CTA, slices [b_lo, b_hi) of one model (all threads call it).
@@ -199,8 +198,6 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   if (tid < kWarps * kDepth) mbar_init(smem_u32(full + tid), 1);
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  constexpr uint32_t rbytes = 32u * (uint32_t)sizeof(RT);   // one slice's R of one objective
-  const int roff = a.wcap * 128;          // R block offset inside a stage
   unsigned char *myring = ring + (size_t)warp * kDepth * pr.stage_bytes;
 
   // 32-bit slice/state indices (the host guarantees |S| + Nc < 2^31)
@@ -225,14 +222,18 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
       wst_s[warp * kDepth + st] = (int)W;
       const uint32_t sbase = ring0 + (uint32_t)(st * pr.stage_bytes);
       const uint32_t fb = bar0 + 8u * (uint32_t)st;
-      const size_t sl = (size_t)(sl0 + j * kWarps);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage
-      mbar_expect_tx(fb, W * 128u + NO * rbytes);
+      mbar_expect_tx(fb, W * 128u);
       if (W) bulk_g2s(sbase, a.pool + (size_t)off * 32, W * 128u, fb);
-#pragma unroll
-      for (int o = 0; o < NO; ++o) bulk_g2s(sbase + (uint32_t)roff + o * rbytes, v.R[o] + sl * 32, rbytes, fb);
     }
     __syncwarp();
+  };
+  // R of my j-th slice, lane = row: one coalesced 128-byte load per objective,
+  // issued one slice ahead of its use
+  auto load_r = [&](int j, RT (&Rr)[NO]) {
+    const size_t sl = (size_t)(sl0 + j * kWarps);
+#pragma unroll
+    for (int o = 0; o < NO; ++o) Rr[o] = __ldg(v.R[o] + sl * 32 + lane);
   };
 
   const int q = lane / a.A_pad, act = lane % a.A_pad;
@@ -247,6 +248,10 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
     r[o] = 0.0;
   }
   for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j, j);
+  RT Rn[NO];   // R of the next slice
+#pragma unroll
+  for (int o = 0; o < NO; ++o) Rn[o] = (RT)0;
+  if (n_mine > 0) load_r(0, Rn);
   int st = 0;
   uint32_t phase = 0;
   int s = sl0 * a.spw + q;                      // state of this lane's row in my j-th slice
@@ -269,7 +274,8 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
     const bool valid = s >= s_lo && s < s_hi && act < a.A;
     RT Rv[NO];
 #pragma unroll
-    for (int o = 0; o < NO; ++o) Rv[o] = reinterpret_cast<const RT *>(sb + roff + o * rbytes)[lane];
+    for (int o = 0; o < NO; ++o) Rv[o] = Rn[o];
+    if (j + 1 < n_mine) load_r(j + 1, Rn);
     const int W = wst_s[warp * kDepth + st];
     Acc<RT> acc[NO];
     // successor layer base of this state; rows without successors (last
@@ -539,7 +545,7 @@ cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStre
 }
 
 cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm) {
-  *stage_bytes = stage_bytes_for(wcap, 4);
+  *stage_bytes = stage_bytes_for(wcap);
   const size_t smem = 256 + (size_t)kWarps * kDepth * (*stage_bytes);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = allow_max_smem((const void *)bellman_batch_kernel);
@@ -571,7 +577,7 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
 
 template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
-  pr->stage_bytes = stage_bytes_for(a.wcap, NO * sizeof(RT));
+  pr->stage_bytes = stage_bytes_for(a.wcap);
   pr->dtab_smem = 0;
   *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
   if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
