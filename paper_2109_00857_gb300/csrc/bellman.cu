@@ -125,6 +125,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// The same copy marked for early L2 eviction (policy from l2_evict_first):
+// the entry stream is read once per sweep and should not push the value
+// tables, which every sweep gathers from, out of L2.
+__device__ __forceinline__ void bulk_g2s_stream(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                                uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 
 constexpr int kWarps = 8;     // warps per CTA
 constexpr int kDepth = 2;     // slices each warp keeps in flight
@@ -205,6 +221,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   const int sl0 = (int)b_lo + warp;                       // my j-th slice: sl0 + j*kWarps
   const uint32_t ring0 = smem_u32(myring), bar0 = smem_u32(full + warp * kDepth);
   uint32_t m_off = 0, m_w = 0;   // lane l: metadata of my slice 32*(j/32) + l
+  const uint64_t stream_policy = l2_evict_first();
 
   // issue(j, st): copy my j-th slice into stage st = j % kDepth (whole warp calls it)
   auto issue = [&](int j, int st) {
@@ -224,7 +241,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
       const uint32_t fb = bar0 + 8u * (uint32_t)st;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage
       mbar_expect_tx(fb, W * 128u);
-      if (W) bulk_g2s(sbase, a.pool + (size_t)off * 32, W * 128u, fb);
+      if (W) bulk_g2s_stream(sbase, a.pool + (size_t)off * 32, W * 128u, fb, stream_policy);
     }
     __syncwarp();
   };
@@ -233,7 +250,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
   auto load_r = [&](int j, RT (&Rr)[NO]) {
     const size_t sl = (size_t)(sl0 + j * kWarps);
 #pragma unroll
-    for (int o = 0; o < NO; ++o) Rr[o] = __ldg(v.R[o] + sl * 32 + lane);
+    for (int o = 0; o < NO; ++o) Rr[o] = __ldcs(v.R[o] + sl * 32 + lane);   // streamed: read once
   };
 
   const int q = lane / a.A_pad, act = lane % a.A_pad;
