@@ -318,6 +318,11 @@ typedef struct {
   double tol;                    /* 0: the exact fixed point by one layered pass (the
                                     Jacobi fixed point bit for bit); > 0: Jacobi sweeps
                                     until the residual is <= tol */
+  int32_t start_t;               /* time step of the start, 0..nt-1: the request replans the
+                                    remaining horizon t = start_t..nt-1 on the resident
+                                    fields with freshly drawn coefficients (on-board
+                                    re-planning, Sec. V); its V / policy cover those
+                                    nt - start_t layers (index (t - start_t)*nx*ny + c) */
 } mdp_request;
 
 typedef struct {

@@ -81,13 +81,14 @@ namespace {
 // Device memory a request holds at its peak (the build's first pool guess of
 // 16 columns per slice, rows, R, classes, V pair, policy, coefficients).
 int64_t estimate_bytes(const EnvEntry &e, const mdp_request &r) {
-  const int64_t nS = (int64_t)e.grid.nx * e.grid.ny * e.grid.nt;
+  const int64_t nt = e.grid.nt - r.start_t;
+  const int64_t nS = (int64_t)e.grid.nx * e.grid.ny * nt;
   int A = e.actions.n_headings * e.actions.n_speeds, A_pad = 1;
   while (A_pad < A) A_pad <<= 1;
   const int64_t spw = 32 / A_pad, n_slices = (nS + spw - 1) / spw, rows = n_slices * 32;
   const int64_t pool = n_slices * 16 * 128;
   return pool + rows * (1 + 2 + 4) + n_slices * 5 + nS * (1 + 4 + 4 + 2) +
-         (int64_t)e.grid.nt * r.N * e.K * 4 + (int64_t)e.grid.nx * e.grid.ny + (1 << 20);
+         nt * r.N * e.K * 4 + (int64_t)e.grid.nx * e.grid.ny + (1 << 20);
 }
 
 __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0, int w, int h) {
@@ -106,21 +107,26 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
                                                              r.target_w, r.target_h);
   std::vector<double> sig(e.sigma);
   for (double &x : sig) x *= r.sigma_scale;
+  // the remaining horizon t = start_t..nt-1: the resident fields from layer
+  // start_t on (float data, layer-major), coefficients drawn afresh
+  const size_t Nc = (size_t)nx * ny, t0 = (size_t)r.start_t;
+  mdp_grid grid = e.grid;
+  grid.nt = e.grid.nt - r.start_t;
   mdp_env env{};
   env.K = e.K;
   env.precision = MDP_FP32;
-  env.vbar = e.vbar;
-  env.modes = e.modes;
+  env.vbar = static_cast<const float *>(e.vbar) + t0 * Nc * 2;
+  env.modes = e.modes ? static_cast<const float *>(e.modes) + t0 * (size_t)e.K * Nc * 2 : nullptr;
   env.coeffs = nullptr;
   env.sigma_h = sig.data();
   env.seed = r.seed;
   env.mdp_id = 0;
-  env.gbar = e.gbar;
-  env.obstacle = e.obstacle;
+  env.gbar = e.gbar ? static_cast<const float *>(e.gbar) + t0 * Nc : nullptr;
+  env.obstacle = e.obstacle + t0 * Nc;
   env.target = tgt;
   const int32_t obj = r.objective;
   mdp_model m = nullptr;
-  mdp_status s = mdp_build(&env, &e.grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m);
+  mdp_status s = mdp_build(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m);
   if (s != MDP_OK) {
     job.status = s;
     job.error = mdp_last_error();
@@ -319,7 +325,7 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   if (req->N < 1 || req->N > 65535 || req->objective < 0 || req->objective > 2 ||
       (req->objective == MDP_OBJ_NET_ENERGY && !e.gbar) || !(req->sigma_scale >= 0) ||
       req->start_i < 0 || req->start_i >= g.nx || req->start_j < 0 || req->start_j >= g.ny ||
-      req->target_w < 1 || req->target_h < 1) {
+      req->target_w < 1 || req->target_h < 1 || req->start_t < 0 || req->start_t >= g.nt) {
     set_error("invalid argument: bad request fields");
     return MDP_ERR_ARG;
   }

@@ -78,7 +78,8 @@ class MdpRequest(C.Structure):
     _fields_ = [("env_id", C.c_int32), ("start_i", C.c_int32), ("start_j", C.c_int32),
                 ("target_i", C.c_int32), ("target_j", C.c_int32), ("target_w", C.c_int32),
                 ("target_h", C.c_int32), ("sigma_scale", C.c_double), ("seed", C.c_uint64),
-                ("N", C.c_int32), ("objective", C.c_int32), ("tol", C.c_double)]
+                ("N", C.c_int32), ("objective", C.c_int32), ("tol", C.c_double),
+                ("start_t", C.c_int32)]
 
 
 class MdpResult(C.Structure):
@@ -366,6 +367,7 @@ class Server:
                "mdp_serve_create")
         self.handle = h.value
         self._envs = []
+        self._start_t = {}
 
     def register(self, denv: DeviceEnv, subgrid_L: Optional[int] = None) -> int:
         e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
@@ -378,15 +380,17 @@ class Server:
         return eid.value
 
     def submit(self, env_id, start, target, target_size=(2, 2), sigma_scale=1.0, seed=0, N=1000,
-               objective=MDP_OBJ_TIME, tol=0.0) -> int:
+               objective=MDP_OBJ_TIME, tol=0.0, start_t=0) -> int:
         r = MdpRequest()
         r.env_id = env_id
         r.start_i, r.start_j = start
         r.target_i, r.target_j = target
         r.target_w, r.target_h = target_size
         r.sigma_scale, r.seed, r.N, r.objective, r.tol = sigma_scale, seed, N, objective, tol
+        r.start_t = start_t
         t = C.c_uint64()
         _check(load().mdp_serve_submit(self.handle, C.byref(r), C.byref(t)), "mdp_serve_submit")
+        self._start_t[t.value] = start_t
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 0, env_id: Optional[int] = None, want_V=False):
@@ -396,8 +400,9 @@ class Server:
         V = pi = None
         if want_V:
             env = self._envs[env_id]
-            V = np.empty(env.nS + 1, dtype=np.float32)
-            pi = np.empty(env.nS, dtype=np.int16)
+            nS = (env.nt - self._start_t.get(int(ticket), 0)) * env.Nc
+            V = np.empty(nS + 1, dtype=np.float32)
+            pi = np.empty(nS, dtype=np.int16)
         code = load().mdp_serve_poll(self.handle, int(ticket), int(timeout_ms), C.byref(res),
                                      V.ctypes.data_as(P) if V is not None else None,
                                      pi.ctypes.data_as(P) if pi is not None else None)

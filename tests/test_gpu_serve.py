@@ -126,3 +126,29 @@ def test_poll_pending_and_unknown_ticket(mdp):
         s.poll(t, timeout_ms=0)      # released after the first successful poll
     assert ei.value.code == -9
     s.close()
+
+
+def test_replanning_from_a_later_time_step(mdp):
+    """A request with start_t = t0 replans the remaining horizon on the
+    resident fields: it equals a direct build + solve of the environment cut
+    to layers t0..nt-1 with the same target, variance scale, seed and N."""
+    env = _env()
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    srv = mdp.Server(8 << 30, 2)
+    eid = srv.register(d)
+    t0 = 5
+    probe = dict(start=(9, 22), target=(30, 8), sigma_scale=0.8, seed=404, N=250, objective=1)
+    t = srv.submit(eid, start_t=t0, **probe)
+    res, V, pi = srv.poll(t, timeout_ms=60000, env_id=eid, want_V=True)
+    assert res.status == 0, mdp.load().mdp_last_error().decode()
+    srv.close()
+    cut = inputs.Environment(**{**env.__dict__})
+    cut.nt = env.nt - t0
+    cut.vbar, cut.modes, cut.obstacle = env.vbar[t0:], env.modes[t0:], env.obstacle[t0:]
+    cut.gbar = env.gbar[t0:] if env.gbar is not None else None
+    Vd, pid = _direct(mdp, cut, probe["target"], probe["sigma_scale"], probe["seed"], probe["N"],
+                      probe["objective"])
+    assert V.shape == Vd.shape == (cut.nS + 1,)
+    assert np.array_equal(V, Vd) and np.array_equal(pi, pid)
+    s0 = probe["start"][1] * env.nx + probe["start"][0]
+    assert res.V_start == V[s0] and res.pi_start == pi[s0]
