@@ -58,6 +58,16 @@ class Problem(C.Structure):
     ]
 
 
+class Problem3D(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nt", C.c_int32),
+                ("dx", C.c_double), ("dt", C.c_double),
+                ("K", C.c_int32), ("N", C.c_int32), ("A", C.c_int32), ("L", C.c_int32),
+                ("vbar", C.c_void_p), ("modes", C.c_void_p), ("Y", C.c_void_p), ("gbar", C.c_void_p),
+                ("obstacle", C.c_void_p), ("target", C.c_void_p), ("act", C.c_void_p),
+                ("c_f", C.c_double), ("c_r", C.c_double), ("r_term", C.c_double),
+                ("r_outbound", C.c_double)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -83,6 +93,9 @@ def lib():
             l.orc_vi_backward.restype = C.c_int
             l.orc_q_values.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P, P]
             l.orc_rollout.argtypes = [C.POINTER(Problem), P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P, P]
+            l.orc_build3d.argtypes = [C.POINTER(Problem3D), C.c_int64, C.c_int64, C.c_int32, P,
+                                      C.c_int32, P, P, P, P, P]
+            l.orc_build3d.restype = C.c_int
             l.orc_rollout.restype = C.c_int
             _lib = l
     return _lib
@@ -297,3 +310,67 @@ def rollout(env, policy, start, objs=(OBJ_TIME,), with_traj=False):
     if st != 0:
         raise ValueError(f"oracle rollout rejected its arguments ({st})")
     return ret, steps, status, traj
+
+
+# ---------------------------------------------------------------- 3-D grid --
+def build3d(env, objs=(OBJ_TIME,), max_nnz=None) -> OracleModel:
+    """The 3-D build (inputs.Environment3D), reordered into the paper layout
+    row = a*|S| + s."""
+    keep = []
+
+    def hold(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    p = Problem3D()
+    p.nx, p.ny, p.nz, p.nt = env.nx, env.ny, env.nz, env.nt
+    p.dx, p.dt = env.dx, env.dt
+    p.K, p.N, p.A, p.L = env.K, env.N, env.A, env.L
+    p.vbar = _p(hold(env.vbar, np.float64))
+    p.modes = _p(hold(env.modes, np.float64))
+    Y = env.Y if env.Y is not None else coeffs_for(env)
+    p.Y = _p(hold(Y, np.float64))
+    p.gbar = _p(hold(env.gbar, np.float64))
+    p.obstacle = _p(hold(env.obstacle, np.uint8))
+    p.target = _p(hold(env.target, np.uint8))
+    p.act = _p(hold(env.actions, np.float64))
+    p.c_f, p.c_r, p.r_term, p.r_outbound = env.c_f, env.c_r, env.r_term, env.r_outbound
+    nS, A = env.nS, env.A
+    if max_nnz is None:
+        max_nnz = env.L ** 3 + 1
+    rows = nS * A
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    nnz = np.zeros(rows, dtype=np.int32)
+    col = np.zeros(rows * max_nnz, dtype=np.int64)
+    cnt = np.zeros(rows * max_nnz, dtype=np.int32)
+    R = np.zeros(len(ob) * rows, dtype=np.float64)
+    ovf = C.c_int64(0)
+    st = lib().orc_build3d(C.byref(p), 0, nS, max_nnz, _p(ob), len(ob), _p(nnz), _p(col), _p(cnt), _p(R),
+                           C.byref(ovf))
+    if st != 0:
+        raise RuntimeError(f"oracle 3-D build failed with status {st}")
+    nnz_local = nnz.reshape(nS, A)
+    rowptr = np.zeros(A * nS + 1, dtype=np.int64)
+    np.cumsum(np.ascontiguousarray(nnz_local.T).reshape(-1), out=rowptr[1:])
+    colp = np.zeros(rowptr[-1], dtype=np.int64)
+    cntp = np.zeros(rowptr[-1], dtype=np.int32)
+    colL = col.reshape(nS, A, max_nnz)
+    cntL = cnt.reshape(nS, A, max_nnz)
+    for a in range(A):
+        for s_idx in np.nonzero(nnz_local[:, a])[0]:
+            r = a * nS + s_idx
+            n = nnz_local[s_idx, a]
+            colp[rowptr[r]:rowptr[r] + n] = colL[s_idx, a, :n]
+            cntp[rowptr[r]:rowptr[r] + n] = cntL[s_idx, a, :n]
+    nobj = len(objs)
+    Rp = np.ascontiguousarray(R.reshape(nobj, nS, A).transpose(0, 2, 1)).reshape(nobj, A * nS)
+    return OracleModel(nS, A, rowptr, colp, cntp, env.N, Rp, None, ovf.value)
+
+
+def fixed_mask3d(env) -> np.ndarray:
+    """1 for 3-D start states whose policy is undefined (targets, obstacles)."""
+    tgt = np.broadcast_to(env.target[None], env.obstacle.shape)
+    return ((env.obstacle != 0) | (tgt != 0)).astype(np.uint8).reshape(-1)

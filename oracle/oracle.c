@@ -403,3 +403,123 @@ int orc_rollout(const orc_problem *p, const int32_t *policy, int32_t i0, int32_t
   }
   return 0;
 }
+
+/* -------------------------------------------------------------- 3-D grid -- */
+/* The 3-D build: the 2-D steps with a third spatial component everywhere. */
+static double step_reward3d(const orc_problem3d *p, int32_t obj, double F, double g_s, double g_sp,
+                            int is_target) {
+  double r;
+  if (obj == ORC_OBJ_TIME) {
+    r = -p->dt;
+  } else if (obj == ORC_OBJ_ENERGY) {
+    double eF = p->c_f * F * F;
+    r = -eF * p->dt;
+  } else {
+    double eF = p->c_f * F * F;
+    double half_cr = 0.5 * p->c_r;
+    r = ((-eF + half_cr * g_s) + half_cr * g_sp) * p->dt;
+  }
+  if (is_target) r = r + p->r_term;
+  return r;
+}
+
+int orc_build3d(const orc_problem3d *p, int64_t u_begin, int64_t u_end, int32_t max_nnz,
+                const int32_t *objs, int32_t n_obj, int32_t *nnz, int64_t *col, int32_t *cnt,
+                double *R, int64_t *overflow) {
+  if (p->L < 1 || (p->L % 2) == 0 || p->A < 1 || p->N < 1 || n_obj < 1 || n_obj > 3) return -2;
+  for (int32_t o = 0; o < n_obj; ++o)
+    if (objs[o] < 0 || objs[o] > 2 || (objs[o] == ORC_OBJ_NET_ENERGY && p->gbar == NULL)) return -2;
+  const int64_t Nx = p->nx, Ny = p->ny, Nz = p->nz, Nt = p->nt, Nc = Nx * Ny * Nz, nS = Nt * Nc;
+  const int32_t L = p->L, h = (L - 1) / 2, A = p->A, K = p->K, N = p->N;
+  const int64_t nb = (int64_t)L * L * L;
+  const int64_t rows = (u_end - u_begin) * A;
+  int32_t *hist = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+  if (!hist) return -2;
+  int status = 0;
+  *overflow = 0;
+  for (int64_t u = u_begin; u < u_end && status == 0; ++u) {
+    const int64_t t = u / Nc, c = u % Nc, i = c % Nx, j = (c / Nx) % Ny, k = c / (Nx * Ny);
+    const int64_t s = t * Nc + c;
+    const int start_terminal = p->target[c] != 0;
+    const int start_obstacle = p->obstacle[s] != 0;
+    const int horizon = (t == Nt - 1);
+    for (int32_t a = 0; a < A; ++a) {
+      const int64_t lr = (u - u_begin) * A + a;
+      int64_t *rc = col + lr * max_nnz;
+      int32_t *rn = cnt + lr * max_nnz;
+      if (start_terminal) {
+        nnz[lr] = 0;
+        for (int32_t o = 0; o < n_obj; ++o) R[o * rows + lr] = 0.0;
+        continue;
+      }
+      if (start_obstacle || horizon) {
+        if (max_nnz < 1) { status = -1; break; }
+        nnz[lr] = 1;
+        rc[0] = nS;
+        rn[0] = N;
+        for (int32_t o = 0; o < n_obj; ++o) R[o * rows + lr] = ((double)N / (double)N) * p->r_outbound;
+        continue;
+      }
+      const double dxa = p->act[4 * a + 0], dya = p->act[4 * a + 1], dza = p->act[4 * a + 2];
+      const double F = p->act[4 * a + 3];
+      memset(hist, 0, sizeof(int32_t) * (size_t)nb);
+      int32_t sink = 0;
+      const double g_s = p->gbar ? p->gbar[s] : 0.0;
+      for (int32_t w = 0; w < N; ++w) {
+        double vx = p->vbar[3 * s + 0], vy = p->vbar[3 * s + 1], vz = p->vbar[3 * s + 2];
+        const double *yw = p->Y + (t * N + w) * K;
+        for (int32_t q = 0; q < K; ++q) {
+          const double *phi = p->modes + 3 * ((t * K + q) * Nc + c);
+          vx = vx + yw[q] * phi[0];
+          vy = vy + yw[q] * phi[1];
+          vz = vz + yw[q] * phi[2];
+        }
+        const double x = ((double)i + 0.5) * p->dx, y = ((double)j + 0.5) * p->dx;
+        const double z = ((double)k + 0.5) * p->dx;
+        const double xp = x + (vx + dxa) * p->dt, yp = y + (vy + dya) * p->dt, zp = z + (vz + dza) * p->dt;
+        const int64_t ip = (int64_t)floor(xp / p->dx), jp = (int64_t)floor(yp / p->dx);
+        const int64_t kp = (int64_t)floor(zp / p->dx);
+        const int64_t di = ip - i, dj = jp - j, dk = kp - k;
+        if (di < -h || di > h || dj < -h || dj > h || dk < -h || dk > h) {
+          ++*overflow;
+          continue;
+        }
+        if (ip < 0 || ip >= Nx || jp < 0 || jp >= Ny || kp < 0 || kp >= Nz ||
+            p->obstacle[(t + 1) * Nc + (kp * Ny + jp) * Nx + ip]) {
+          ++sink;
+          continue;
+        }
+        ++hist[((dk + h) * L + (dj + h)) * L + (di + h)];
+      }
+      int32_t e = 0;
+      for (int32_t o = 0; o < n_obj; ++o) R[o * rows + lr] = 0.0;
+      for (int64_t b = 0; b < nb; ++b) {
+        if (hist[b] == 0) continue;
+        if (e >= max_nnz) { status = -1; break; }
+        const int64_t dk = b / ((int64_t)L * L) - h, dj = (b / L) % L - h, di = b % L - h;
+        const int64_t ip = i + di, jp = j + dj, kp = k + dk;
+        const int64_t cp = (kp * Ny + jp) * Nx + ip;
+        rc[e] = (t + 1) * Nc + cp;
+        rn[e] = hist[b];
+        const int is_t = p->target[cp] != 0;
+        const double g_sp = p->gbar ? p->gbar[(t + 1) * Nc + cp] : 0.0;
+        const double prob = (double)hist[b] / (double)N;
+        for (int32_t o = 0; o < n_obj; ++o)
+          R[o * rows + lr] = R[o * rows + lr] + prob * step_reward3d(p, objs[o], F, g_s, g_sp, is_t);
+        ++e;
+      }
+      if (status != 0) break;
+      if (sink > 0) {
+        if (e >= max_nnz) { status = -1; break; }
+        rc[e] = nS;
+        rn[e] = sink;
+        const double prob = (double)sink / (double)N;
+        for (int32_t o = 0; o < n_obj; ++o) R[o * rows + lr] = R[o * rows + lr] + prob * p->r_outbound;
+        ++e;
+      }
+      nnz[lr] = e;
+    }
+  }
+  free(hist);
+  return status;
+}

@@ -96,6 +96,30 @@ int orc_vi_backward(int64_t nS, int32_t A, int32_t nt, int64_t Nc, const int64_t
 void orc_q_values(int64_t nS, int32_t A, const int64_t *rowptr, const int64_t *col,
                   const double *prob, const double *R, const double *V, double *Q);
 
+/* ------------------------------------------------------------- 3-D grid --
+ * The same build in 3-D space (Sec. II-A: the formulation holds for n = 3):
+ * cube cells, state s = t*Nc + (k*Ny + j)*Nx + i with Nc = Nx*Ny*Nz, velocity
+ * and action displacements with three components, a cubic neighbouring
+ * sub-grid of side L, bin b = ((dk+h)*L + (dj+h))*L + (di+h). */
+typedef struct {
+  int32_t nx, ny, nz, nt;
+  double dx, dt;
+  int32_t K, N, A, L;
+  const double *vbar;          /* [nt][nz][ny][nx][3] */
+  const double *modes;         /* [nt][K][nz][ny][nx][3] */
+  const double *Y;             /* [nt][N][K] */
+  const double *gbar;          /* [nt][nz][ny][nx] (may be NULL) */
+  const uint8_t *obstacle;     /* [nt][nz][ny][nx] */
+  const uint8_t *target;       /* [nz][ny][nx] */
+  const double *act;           /* [A][4] (d_x, d_y, d_z, F) */
+  double c_f, c_r, r_term, r_outbound;
+} orc_problem3d;
+
+/* orc_build for the 3-D grid: same outputs and return codes (no R_lit). */
+int orc_build3d(const orc_problem3d *p, int64_t u_begin, int64_t u_end, int32_t max_nnz,
+                const int32_t *objs, int32_t n_obj, int32_t *nnz, int64_t *col, int32_t *cnt,
+                double *R, int64_t *overflow);
+
 /* Policy rollouts (Sec. IV: the optimal policy applied to every flow
  * realization from the start).  Path w starts at cell (i0, j0) at t = 0 and
  * follows policy[s] (s = t*Nc + j*Nx + i), moving with realization w's

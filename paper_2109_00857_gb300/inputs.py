@@ -270,3 +270,128 @@ def batch_member(i: int, **kw) -> Environment:
                 mdp_id=i, name=f"batch-{i}")
     args.update(kw)
     return make_env(**args)
+
+
+# ------------------------------------------------------------------ 3-D grid --
+@dataclasses.dataclass
+class Environment3D:
+    """A 3-D environment (Sec. II-A with n = 3): cube cells, three velocity
+    components, actions with a vertical component."""
+    nx: int
+    ny: int
+    nz: int
+    nt: int
+    K: int
+    N: int
+    L: int
+    vbar: np.ndarray          # [nt][nz][ny][nx][3] float64
+    modes: np.ndarray         # [nt][K][nz][ny][nx][3] float64
+    sigma: np.ndarray         # [K] float64
+    seed: int
+    obstacle: np.ndarray      # [nt][nz][ny][nx] uint8
+    target: np.ndarray        # [nz][ny][nx] uint8
+    actions: np.ndarray       # [A][4] float64 (dx_a, dy_a, dz_a, F_a)
+    gbar: Optional[np.ndarray] = None   # [nt][nz][ny][nx] float64
+    Y: Optional[np.ndarray] = None      # [nt][N][K] or None
+    mdp_id: int = 0
+    dx: float = 1.0
+    dt: float = 1.0
+    c_f: float = 1.0
+    c_r: float = 1.0
+    r_term: float = 0.0
+    r_outbound: float = 0.0
+    objectives: tuple = (OBJ_TIME,)
+    name: str = ""
+
+    @property
+    def A(self) -> int:
+        return int(self.actions.shape[0])
+
+    @property
+    def Nc(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nS(self) -> int:
+        return self.nt * self.Nc
+
+    def samples(self) -> int:
+        return self.N * self.A * self.nS
+
+
+def action_table3d(n_headings: int, elevations: Sequence[float], speeds: Sequence[float]) -> np.ndarray:
+    """(F cos e cos theta, F cos e sin theta, F sin e, F) for every speed F,
+    elevation angle e and heading theta_h = 2 pi h / Nh (a = (f*Ne + e)*Nh + h);
+    straight up/down (|e| = pi/2) is listed once per speed."""
+    rows = []
+    for F in speeds:
+        for e in elevations:
+            hs = [0] if abs(abs(e) - math.pi / 2) < 1e-12 else range(n_headings)
+            for h in hs:
+                th = 2.0 * math.pi * h / n_headings
+                rows.append((F * math.cos(e) * math.cos(th), F * math.cos(e) * math.sin(th), F * math.sin(e), F))
+    return np.asarray(rows, dtype=np.float64)
+
+
+def make_env3d(nx, ny, nz, nt, K, N, L, sigma, seed, amplitude, w_amplitude=0.3, n_headings=8,
+               elevations=(-math.pi / 4, 0.0, math.pi / 4), speeds=(1.0,), obstacle_boxes=1,
+               with_gbar=False, objectives=(OBJ_TIME,), r_term=0.0, r_outbound=None, name="",
+               mdp_id=0) -> Environment3D:
+    """Layers of the 2-D double gyre (amplitude decaying with depth), a weak
+    vertical velocity cos(pi z) sin(2 pi x), modes = the 2-D modes with a
+    vertical component sin(pi z) (orthonormalised per step), boxes drifting
+    east, target block near the top, solar field on every layer."""
+    rng = np.random.default_rng(seed)
+    g2 = double_gyre(nx, ny, nt, amplitude)
+    zt = (np.arange(nz) + 0.5) / nz
+    xt = (np.arange(nx) + 0.5) / nx
+    vbar = np.zeros((nt, nz, ny, nx, 3))
+    for k in range(nz):
+        vbar[:, k, :, :, :2] = g2 * (1.0 - 0.5 * zt[k])
+        vbar[:, k, :, :, 2] = w_amplitude * math.cos(math.pi * zt[k]) * np.sin(2 * math.pi * xt)[None, None, :]
+    m2 = do_modes(nx, ny, nt, K)
+    modes = np.zeros((nt, K, nz, ny, nx, 3))
+    for t in range(nt):
+        basis = []
+        for q in range(K):
+            vec = np.zeros((nz, ny, nx, 3))
+            vec[..., :2] = m2[t, q][None] * np.cos(0.5 * math.pi * zt)[:, None, None, None]
+            vec[..., 2] = 0.5 * m2[t, q][None, ..., 0] * np.sin(math.pi * zt)[:, None, None]
+            for b in basis:
+                vec = vec - np.mean(np.sum(vec * b, axis=-1)) * b
+            vec = vec / math.sqrt(np.mean(np.sum(vec * vec, axis=-1)))
+            basis.append(vec)
+            modes[t, q] = vec
+    obs = np.zeros((nt, nz, ny, nx), dtype=np.uint8)
+    for bx in range(obstacle_boxes):
+        y0 = int(rng.integers(ny // 4, max(ny // 4 + 1, 3 * ny // 4 - 2)))
+        z0 = int(rng.integers(0, max(1, nz - 2)))
+        side = max(2, nx // 6)
+        for t in range(nt):
+            x0 = -side + t // 2 + bx * nx // 3
+            xs, xe = max(x0, 0), min(x0 + side, nx)
+            if xs < xe:
+                obs[t, z0:z0 + max(2, nz // 3), y0:y0 + side, xs:xe] = 1
+    tgt = np.zeros((nz, ny, nx), dtype=np.uint8)
+    tgt[nz - 2:nz, int(0.8 * ny):int(0.8 * ny) + 2, nx // 2:nx // 2 + 2] = 1
+    gbar = None
+    if with_gbar:
+        s2 = solar_field(nx, ny, nt, rng)
+        gbar = np.repeat(s2[:, None], nz, axis=1) * (0.5 + 0.5 * zt)[None, :, None, None]
+    if r_outbound is None:
+        r_outbound = -10.0 * nt
+    return Environment3D(nx=nx, ny=ny, nz=nz, nt=nt, K=K, N=N, L=L, vbar=vbar, modes=modes,
+                         sigma=np.asarray(sigma, dtype=np.float64), seed=seed, obstacle=obs, target=tgt,
+                         actions=action_table3d(n_headings, elevations, speeds), gbar=gbar,
+                         mdp_id=mdp_id, r_term=r_term, r_outbound=r_outbound,
+                         objectives=tuple(objectives), name=name)
+
+
+def cube(**kw) -> Environment3D:
+    """3-D instance: 64x64x16 cells, nt = 40, K = 4, N = 1000, 8 headings at
+    elevations -45, 0 and +45 degrees (24 actions), 7x7x7 sub-grid."""
+    args = dict(nx=64, ny=64, nz=16, nt=40, K=4, N=1000, L=7,
+                sigma=tuple(0.15 * 2.0 ** (-q / 2.0) for q in range(4)), seed=61, amplitude=0.8,
+                objectives=(OBJ_TIME,), name="cube-64x64x16x40-N1000-A24")
+    args.update(kw)
+    return make_env3d(**args)
