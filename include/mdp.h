@@ -244,6 +244,44 @@ mdp_status mdp_sample_coeffs(int32_t nt, int32_t N, int32_t K, const double *sig
                              uint64_t seed, uint64_t mdp_id, int32_t precision, void *Y,
                              void *stream);
 
+/* ------------------------------------------------------------- 3-D grid --
+ * The build on a 3-D grid (Sec. II-A: the formulation holds for n = 3).  Cube
+ * cells, state s = t*Nc + (k*ny + j)*nx + i with Nc = nx*ny*nz, a cubic
+ * neighbouring sub-grid of side subgrid_L (odd, 1..11; no automatic size).
+ * The returned model has the 2-D layout (successor offsets dk*nx*ny + dj*nx
+ * + di as signed 16 bits: subgrid half-width * (nx*ny + nx + 1) <= 32767),
+ * so mdp_solve, mdp_solve_multi, mdp_export_csr, mdp_model_info and
+ * mdp_model_free apply unchanged.  FP32 lands with the exact floor of
+ * u + d per axis like the 2-D build; FP64_CHECK follows the oracle's
+ * literal formulas.  Errors as mdp_build. */
+typedef struct {
+  int32_t nx, ny, nz, nt;
+  double dx, dt;
+} mdp_grid3d;
+
+typedef struct {
+  int32_t K;
+  int32_t precision;        /* mdp_precision */
+  const void *vbar;         /* [nt][nz][ny][nx][3] */
+  const void *modes;        /* [nt][K][nz][ny][nx][3] */
+  const void *coeffs;       /* [nt][N][K] or NULL (drawn as in mdp_env) */
+  const double *sigma_h;    /* host [K] */
+  uint64_t seed, mdp_id;
+  const void *gbar;         /* [nt][nz][ny][nx] or NULL */
+  const uint8_t *obstacle;  /* [nt][nz][ny][nx] */
+  const uint8_t *target;    /* [nz][ny][nx] */
+} mdp_env3d;
+
+typedef struct {
+  int32_t A;                /* 1..32 */
+  const double *table_h;    /* host [A][4]: (d_x, d_y, d_z, F) per action */
+  double c_f, c_r, r_term, r_outbound;
+} mdp_actions3d;
+
+mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_actions3d *actions,
+                       int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                       void *stream, mdp_model *out);
+
 /* ------------------------------------------------------------- rollouts --
  * Policy rollouts (Sec. IV: the optimal policy applied to every flow
  * realization from the start; the mean returns are the expected mission

@@ -31,6 +31,7 @@ UNITS = {
     "noalloc.cu": [],
     "batch.cu": [],
     "rollout.cu": [],
+    "build3d.cu": [],
     "check_fp64.cu": ["-fmad=false"],
 }
 

@@ -1,0 +1,516 @@
+// build3d.cu -- the MDP build on a 3-D grid (Sec. II-A with n = 3: the
+// formulation and the implementation hold in 3-D space).  The model it
+// returns has the 2-D model's layout (sliced-ELL rows of signed 16-bit
+// successor offsets dk*Nx*Ny + dj*Nx + di), so mdp_solve, mdp_solve_multi,
+// mdp_export_csr and mdp_model_info apply unchanged.
+//
+// One CTA per slice (spw states x A_pad actions, 32 rows), persistent over a
+// work queue.  Per chunk of realizations the threads form the velocity of
+// their (state, realization) items once for all actions and stage it in
+// shared memory (phase A); then lane l of every warp bins row l's landings of
+// the staged realizations into a full L^3 window hist[bin][l] with a
+// shared-memory reduction (phase B: a lane only touches its own bank); warp 0
+// turns each row's window into ascending entries with the sink folded and
+// R(s,a) from the counts.  FP32 lands with the exact floor of u + d per axis
+// (the 2-D path's landing offsets); FP64 check mode evaluates the oracle's
+// literal formulas in its order without contraction.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "build_common.cuh"
+
+namespace mdpgb {
+
+constexpr int kMaxL3 = 11;   // largest 3-D window side (11^3 bins x 128 B in shared memory)
+
+struct Actions3 {
+  float dl[3][kMaxActions];     // displacement * dt/dx per axis (FP32 kinematics)
+  int32_t c[3][kMaxActions];    // floor(dl)
+  float th[3][kMaxActions];     // smallest float >= 1 - frac(dl) (2: integer dl)
+  float F[kMaxActions];
+  double d64[3][kMaxActions];   // displacement in FP64 (check mode)
+  double F64[kMaxActions];
+};
+
+struct Build3Args {
+  int32_t nx, ny, nz, nt, K, N, A, A_pad, spw, L, h, row_cap, chunk;
+  int64_t Nc, nS, n_slices, rows_pad;
+  float lam;
+  double dx, dt;
+  const void *vbar, *modes, *Y, *gbar;
+  const uint8_t *cls, *target, *obstacle;
+  Actions3 act;
+  RewardParams rw;
+  uint32_t *pool;
+  uint64_t pool_cap_cols;
+  uint32_t *slice_off;
+  uint8_t *slice_w, *nnz;
+  uint16_t *sinkc;
+  void *R;
+  unsigned long long *cnt;
+};
+
+template <typename RT>
+struct U3 {
+  RT x, y, z;
+};
+
+template <typename RT>
+__global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
+  extern __shared__ __align__(16) unsigned char smem3[];
+  const int nb = a.L * a.L * a.L;
+  uint32_t *hist = reinterpret_cast<uint32_t *>(smem3);   // [nb][32]
+  U3<RT> *ubuf = reinterpret_cast<U3<RT> *>(smem3 + (size_t)nb * 128);   // [chunk][spw]
+  __shared__ long long s_slice;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int h = a.h, L = a.L;
+  const int64_t Nc = a.Nc, nxy = (int64_t)a.nx * a.ny;
+  const int q_l = lane / a.A_pad, a_l = lane % a.A_pad;
+  const bool act_ok = a_l < a.A;
+  const int q_t = tid % a.spw, w0 = tid / a.spw, wstride = blockDim.x / a.spw;
+  const RT *vbar = static_cast<const RT *>(a.vbar);
+  const RT *modes = static_cast<const RT *>(a.modes);
+  const RT *Yall = static_cast<const RT *>(a.Y);
+  for (int i = tid; i < nb * 32; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_slice = (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+    __syncthreads();
+    const int64_t sl = s_slice;
+    if (sl >= a.n_slices) break;
+    const int64_t s_l = sl * a.spw + q_l, s_t = sl * a.spw + q_t;
+    // state kinds: terminal first, then obstacle start or last layer, else sampled
+    auto kind = [&](int64_t s) {
+      if (s >= a.nS) return (int)KIND_NONE;
+      if (a.target[s % Nc]) return (int)KIND_TERMINAL;
+      if (a.obstacle[s] || s / Nc == a.nt - 1) return (int)KIND_SINK;
+      return (int)KIND_SAMPLE;
+    };
+    int kind_l = act_ok ? kind(s_l) : KIND_NONE;
+    const int kind_t = kind(s_t);
+    const int any = __syncthreads_or(kind_t == KIND_SAMPLE);
+    if (any) {
+      const int64_t t = s_t / Nc, c = s_t % Nc;
+      const RT *Yt = Yall + (size_t)t * a.N * a.K;
+      for (int c0 = 0; c0 < a.N; c0 += a.chunk) {
+        const int cn = min(a.chunk, a.N - c0);
+        // ---- phase A: velocity of (state q_t, realization w) once for all actions
+        for (int w = w0; w < cn; w += wstride) {
+          if (kind_t != KIND_SAMPLE) continue;
+          const RT *yw = Yt + (size_t)(c0 + w) * a.K;
+          U3<RT> u;
+          if constexpr (sizeof(RT) == 4) {
+            float vx = vbar[3 * s_t], vy = vbar[3 * s_t + 1], vz = vbar[3 * s_t + 2];
+            for (int k = 0; k < a.K; ++k) {
+              const float *ph = modes + 3 * ((t * a.K + k) * Nc + c);
+              vx = fmaf(yw[k], ph[0], vx);
+              vy = fmaf(yw[k], ph[1], vy);
+              vz = fmaf(yw[k], ph[2], vz);
+            }
+            u.x = fmaf(vx, a.lam, 0.5f);
+            u.y = fmaf(vy, a.lam, 0.5f);
+            u.z = fmaf(vz, a.lam, 0.5f);
+            if (!(fabsf(u.x) < 1e30f)) u.x = 1e30f;
+            if (!(fabsf(u.y) < 1e30f)) u.y = 1e30f;
+            if (!(fabsf(u.z) < 1e30f)) u.z = 1e30f;
+          } else {
+            double vx = vbar[3 * s_t], vy = vbar[3 * s_t + 1], vz = vbar[3 * s_t + 2];
+            for (int k = 0; k < a.K; ++k) {
+              const double *ph = modes + 3 * ((t * a.K + k) * Nc + c);
+              vx = __dadd_rn(vx, __dmul_rn(yw[k], ph[0]));
+              vy = __dadd_rn(vy, __dmul_rn(yw[k], ph[1]));
+              vz = __dadd_rn(vz, __dmul_rn(yw[k], ph[2]));
+            }
+            u.x = vx;   // the velocity itself: the landing adds the position and action
+            u.y = vy;
+            u.z = vz;
+          }
+          ubuf[(size_t)w * a.spw + q_t] = u;
+        }
+        __syncthreads();
+        // ---- phase B: lane l bins row l's landings of the staged realizations
+        if (kind_l == KIND_SAMPLE) {
+          const int64_t sc = s_l % Nc;
+          const int64_t li = sc % a.nx, lj = (sc / a.nx) % a.ny, lk = sc / nxy;
+          const uint32_t hb = smem_u32(hist) + (uint32_t)lane * 4u;
+          for (int w = warp; w < cn; w += nwarps) {
+            const U3<RT> u = ubuf[(size_t)w * a.spw + q_l];
+            int di, dj, dk;
+            if constexpr (sizeof(RT) == 4) {
+              di = land_offset(u.x, a.act.c[0][a_l], a.act.th[0][a_l]);
+              dj = land_offset(u.y, a.act.c[1][a_l], a.act.th[1][a_l]);
+              dk = land_offset(u.z, a.act.c[2][a_l], a.act.th[2][a_l]);
+            } else {
+              // x' = x + (v + a) dt from the cell centre, cell() = floor(x' / dx)
+              const double x = __dmul_rn((double)li + 0.5, a.dx), y = __dmul_rn((double)lj + 0.5, a.dx);
+              const double z = __dmul_rn((double)lk + 0.5, a.dx);
+              const double xp = __dadd_rn(x, __dmul_rn(__dadd_rn(u.x, a.act.d64[0][a_l]), a.dt));
+              const double yp = __dadd_rn(y, __dmul_rn(__dadd_rn(u.y, a.act.d64[1][a_l]), a.dt));
+              const double zp = __dadd_rn(z, __dmul_rn(__dadd_rn(u.z, a.act.d64[2][a_l]), a.dt));
+              const double fx = floor(__ddiv_rn(xp, a.dx)) - (double)li;
+              const double fy = floor(__ddiv_rn(yp, a.dx)) - (double)lj;
+              const double fz = floor(__ddiv_rn(zp, a.dx)) - (double)lk;
+              di = (fabs(fx) <= (double)h) ? (int)fx : h + 1;
+              dj = (fabs(fy) <= (double)h) ? (int)fy : h + 1;
+              dk = (fabs(fz) <= (double)h) ? (int)fz : h + 1;
+            }
+            if (di < -h || di > h || dj < -h || dj > h || dk < -h || dk > h) {
+              atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
+              continue;
+            }
+            const uint32_t b = (uint32_t)(((dk + h) * L + (dj + h)) * L + (di + h));
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + b * 128u), "r"(1u));
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- emit (warp 0): ascending bins (dk, dj, di), sink folded, R from counts
+    if (warp == 0) {
+      const int64_t ir = sl * 32 + lane;
+      const int64_t t = s_l / Nc, c = s_l % Nc;
+      const int64_t li = c % a.nx, lj = (c / a.nx) % a.ny, lk = c / nxy;
+      const int64_t nxt = (t + 1) * Nc;
+      int e = 0;
+      uint32_t sink = 0;
+      if (kind_l == KIND_SAMPLE) {
+        for (int b = 0; b < nb; ++b) {
+          const uint32_t n = hist[b * 32 + lane];
+          if (!n) continue;
+          const int64_t ip = li + (b % L) - h, jp = lj + (b / L) % L - h, kp = lk + b / (L * L) - h;
+          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+          if (!inside || a.obstacle[nxt + (kp * a.ny + jp) * a.nx + ip]) sink += n;
+          else ++e;
+        }
+      } else if (kind_l == KIND_SINK) {
+        sink = (uint32_t)a.N;
+      }
+      const bool cap_hit = e + (sink > 0 ? 1 : 0) > a.row_cap;
+      if (cap_hit) {
+        atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
+        e = 0;
+      }
+      int W = e;
+      for (int off = 16; off > 0; off >>= 1) W = max(W, __shfl_xor_sync(0xffffffffu, W, off));
+      unsigned long long base = 0;
+      if (lane == 0 && W > 0) base = atomicAdd(&a.cnt[CNT_POOL_COLS], (unsigned long long)W);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const bool fits = (W == 0) || (base + (unsigned long long)W <= a.pool_cap_cols);
+      if (!fits && lane == 0) atomicAdd(&a.cnt[CNT_POOL_FULL], 1ULL);
+      const bool write = fits && !cap_hit;
+      RT Racc[3] = {0, 0, 0};
+      uint32_t *dst = a.pool + base * 32 + lane;
+      int k = 0;
+      if (kind_l == KIND_SAMPLE) {
+        const RT F = sizeof(RT) == 4 ? (RT)a.act.F[a_l] : (RT)a.act.F64[a_l];
+        const RT g_s = a.gbar ? static_cast<const RT *>(a.gbar)[s_l] : (RT)0;
+        for (int b = 0; b < nb; ++b) {
+          uint32_t *hp = hist + b * 32 + lane;
+          const uint32_t n = *hp;
+          if (!n) continue;
+          *hp = 0;
+          const int di = b % L - h, dj = (b / L) % L - h, dk = b / (L * L) - h;
+          const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
+          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+          const int64_t cp = (kp * a.ny + jp) * a.nx + ip;
+          if (!inside || a.obstacle[nxt + cp]) continue;
+          if (write) dst[(size_t)k * 32] = entry_word((int)(dk * nxy + dj * a.nx + di), n);
+          ++k;
+          const bool is_t = a.target[cp] != 0;
+          const RT g_sp = a.gbar ? static_cast<const RT *>(a.gbar)[nxt + cp] : (RT)0;
+          for (int o = 0; o < a.rw.n_obj; ++o) {
+            if constexpr (sizeof(RT) == 4) {
+              Racc[o] = fmaf((float)n / (float)a.N, step_reward32(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t), Racc[o]);
+            } else {
+              const double p = __ddiv_rn((double)n, (double)a.N);
+              Racc[o] = __dadd_rn(Racc[o], __dmul_rn(p, step_reward64(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t)));
+            }
+          }
+        }
+        if (sink) {
+          for (int o = 0; o < a.rw.n_obj; ++o) {
+            if constexpr (sizeof(RT) == 4)
+              Racc[o] = fmaf((float)sink / (float)a.N, (float)a.rw.r_out, Racc[o]);
+            else
+              Racc[o] = __dadd_rn(Racc[o], __dmul_rn(__ddiv_rn((double)sink, (double)a.N), a.rw.r_out));
+          }
+        }
+      } else if (kind_l == KIND_SINK) {
+        for (int o = 0; o < a.rw.n_obj; ++o)
+          Racc[o] = sizeof(RT) == 4 ? (RT)(float)a.rw.r_out : (RT)__dmul_rn(__ddiv_rn((double)a.N, (double)a.N), a.rw.r_out);
+      }
+      if (!write) {
+        e = 0;
+        k = 0;
+      }
+      if (write)
+        for (int kk = k; kk < W; ++kk) dst[(size_t)kk * 32] = 0u;
+      if (!fits) sink = 0;
+      if (lane == 0) {
+        a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
+        a.slice_w[sl] = (fits && W > 0) ? (uint8_t)W : (uint8_t)0;
+      }
+      a.nnz[ir] = (uint8_t)e;
+      a.sinkc[ir] = (uint16_t)sink;
+      for (int o = 0; o < a.rw.n_obj; ++o) static_cast<RT *>(a.R)[(int64_t)o * a.rows_pad + ir] = Racc[o];
+      int dom = e, tot = e + (sink > 0 ? 1 : 0);
+      for (int off = 16; off > 0; off >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, off);
+        dom += __shfl_xor_sync(0xffffffffu, dom, off);
+      }
+      const int sampled = __popc(__ballot_sync(0xffffffffu, kind_l == KIND_SAMPLE));
+      if (lane == 0) {
+        atomicAdd(&a.cnt[CNT_NNZ], (unsigned long long)tot);
+        atomicAdd(&a.cnt[CNT_DOMAIN], (unsigned long long)dom);
+        atomicAdd(&a.cnt[CNT_SAMPLES], (unsigned long long)sampled * (unsigned long long)a.N);
+        atomicMax(&a.cnt[CNT_MAXROW], (unsigned long long)W);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// FP32 landing-offset constants of one axis (same rule as the 2-D tables).
+static void axis_constants(const float *d, int A, int32_t *c, float *th) {
+  for (int a = 0; a < A; ++a) {
+    const double dd = (double)d[a], fl = std::floor(dd);
+    c[a] = (int32_t)fl;
+    if (dd == fl) {
+      th[a] = 2.0f;
+    } else {
+      const double t1 = (fl + 1.0) - dd;
+      float f = (float)t1;
+      if ((double)f < t1) f = std::nextafter(f, 2.0f);
+      th[a] = f;
+    }
+  }
+}
+
+}  // namespace mdpgb
+
+using namespace mdpgb;
+
+static mdp_status arg3(const char *msg) {
+  set_error(std::string("invalid argument: ") + msg);
+  return MDP_ERR_ARG;
+}
+
+extern "C" mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_actions3d *actions,
+                                  int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                                  void *stream, mdp_model *out) {
+  if (!out) return arg3("out is NULL");
+  *out = nullptr;
+  mdp_status s = check_device();
+  if (s != MDP_OK) return s;
+  if (!env || !grid || !actions || !objs_h) return arg3("NULL pointer");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nt < 1 || !(grid->dx > 0) || !(grid->dt > 0))
+    return arg3("grid");
+  if (N < 1 || N > 65535) return arg3("N must be in [1, 65535]");
+  if (subgrid_L < 1 || subgrid_L > kMaxL3 || subgrid_L % 2 == 0) return arg3("subgrid_L must be odd in [1, 11]");
+  if (n_obj < 1 || n_obj > 3) return arg3("n_obj must be 1, 2 or 3");
+  if (env->K < 0 || env->K > kMaxModes) return arg3("K");
+  if (env->precision != MDP_FP32 && env->precision != MDP_FP64_CHECK) return arg3("precision");
+  if (!env->vbar || !env->obstacle || !env->target || (env->K > 0 && !env->modes))
+    return arg3("vbar, modes, obstacle and target must be non-NULL");
+  if (env->K > 0 && !env->coeffs && !env->sigma_h) return arg3("need coeffs or sigma_h");
+  for (int o = 0; o < n_obj; ++o) {
+    if (objs_h[o] < 0 || objs_h[o] > 2) return arg3("unknown objective");
+    if (objs_h[o] == MDP_OBJ_NET_ENERGY && !env->gbar) return arg3("net energy needs gbar");
+  }
+  const int A = actions->A;
+  if (A < 1 || A > kMaxActions || !actions->table_h) return arg3("A must be in [1, 32] with a table");
+  const int h = (subgrid_L - 1) / 2;
+  const int64_t nxy = (int64_t)grid->nx * grid->ny;
+  if ((int64_t)h * (nxy + grid->nx + 1) > 32767)
+    return arg3("sub-grid half-width * (nx*ny + nx + 1) must be <= 32767 (16-bit successor offsets)");
+  const int prec = env->precision;
+  const size_t fsz = prec == MDP_FP64_CHECK ? 8 : 4;
+  const double lam = grid->dt / grid->dx;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  Build3Args ba;
+  memset(&ba, 0, sizeof(ba));
+  for (int a = 0; a < A; ++a) {
+    for (int x = 0; x < 3; ++x) {
+      const double d = actions->table_h[4 * a + x];
+      if (!std::isfinite(d)) return arg3("action table holds a non-finite value");
+      ba.act.d64[x][a] = d;
+      ba.act.dl[x][a] = (float)(d * lam);
+    }
+    ba.act.F64[a] = actions->table_h[4 * a + 3];
+    ba.act.F[a] = (float)actions->table_h[4 * a + 3];
+  }
+  for (int x = 0; x < 3; ++x) axis_constants(ba.act.dl[x], A, ba.act.c[x], ba.act.th[x]);
+
+  mdp_model_t *m = new mdp_model_t();
+  memset(m, 0, sizeof(*m));
+  auto fail = [&](mdp_status code) {
+    cudaStreamSynchronize(st);
+    free_model_on_stream(m, st);
+    return code;
+  };
+#define TRY3(expr)                                                \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return fail(cuda_fail(_e, #expr));     \
+  } while (0)
+  cudaGetDevice(&m->device);
+  m->nx = grid->nx; m->ny = (int32_t)(grid->ny * grid->nz); m->nt = grid->nt;   // Nc = nx * (ny * nz)
+  m->K = env->K; m->N = N; m->A = A; m->precision = prec; m->n_obj = n_obj;
+  for (int o = 0; o < n_obj; ++o) m->objs[o] = objs_h[o];
+  m->Nc = nxy * grid->nz; m->nS = m->Nc * grid->nt; m->dx = grid->dx; m->dt = grid->dt;
+  int A_pad = 1;
+  while (A_pad < A) A_pad <<= 1;
+  m->A_pad = A_pad;
+  m->spw = 32 / A_pad;
+  m->n_slices = (m->nS + m->spw - 1) / m->spw;
+  m->rows_pad = m->n_slices * 32;
+  m->L = subgrid_L;
+  m->h = h;
+  m->nbins = subgrid_L * subgrid_L * subgrid_L;
+  const int row_cap = std::min(255, m->nbins + 1);
+  m->row_cap = row_cap;
+  RewardParams rw;
+  memset(&rw, 0, sizeof(rw));
+  rw.c_f = actions->c_f; rw.c_r = actions->c_r; rw.r_term = actions->r_term;
+  rw.r_out = actions->r_outbound; rw.dt = grid->dt; rw.dx = grid->dx; rw.n_obj = n_obj;
+  for (int o = 0; o < n_obj; ++o) rw.objs[o] = objs_h[o];
+  m->rw = rw;
+
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  cudaEventRecord(ev0, st);
+  TRY3(dev_alloc((void **)&m->cnt, sizeof(unsigned long long) * CNT_N, st));
+  TRY3(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
+  const void *Y = env->coeffs;
+  void *Yown = nullptr;
+  double *sig_d = nullptr;
+  int launches = 0;
+  if (!Y && env->K > 0) {
+    TRY3(dev_alloc(&Yown, fsz * (size_t)grid->nt * N * env->K, st));
+    TRY3(dev_alloc((void **)&sig_d, sizeof(double) * env->K, st));
+    TRY3(cudaMemcpyAsync(sig_d, env->sigma_h, sizeof(double) * env->K, cudaMemcpyHostToDevice, st));
+    TRY3(launch_sample_coeffs(grid->nt, N, env->K, sig_d, env->seed, env->mdp_id,
+                              prec == MDP_FP64_CHECK ? (double *)Yown : nullptr,
+                              prec == MDP_FP32 ? (float *)Yown : nullptr, m->cnt + CNT_CAPPED, st));
+    Y = Yown;
+    ++launches;
+  }
+  auto release = [&]() {
+    dev_free(Yown, st);
+    dev_free(sig_d, st);
+    Yown = nullptr;
+    sig_d = nullptr;
+  };
+  // model memory: the entry pool sized for 8 columns per slice first, rebuilt
+  // once with the worst case if that runs out
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const uint64_t budget_cols = (uint64_t)(0.6 * (double)free_b) / 128;
+  auto cols_for = [&](int width) {
+    uint64_t c = (uint64_t)m->n_slices * (uint64_t)std::min(width, row_cap) + 64;
+    return std::max<uint64_t>(1, std::min(c, budget_cols));
+  };
+  uint64_t cap_cols = cols_for(8);
+  TRY3(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+  TRY3(dev_alloc((void **)&m->slice_off, sizeof(uint32_t) * (size_t)m->n_slices, st));
+  TRY3(dev_alloc((void **)&m->slice_w, (size_t)m->n_slices, st));
+  TRY3(dev_alloc((void **)&m->nnz, (size_t)m->rows_pad, st));
+  TRY3(dev_alloc((void **)&m->sinkc, sizeof(uint16_t) * (size_t)m->rows_pad, st));
+  TRY3(dev_alloc(&m->R, fsz * (size_t)m->rows_pad * n_obj, st));
+  TRY3(dev_alloc((void **)&m->cls, (size_t)m->nS, st));
+  TRY3(dev_alloc((void **)&m->delta, sizeof(int32_t) * (size_t)subgrid_L * subgrid_L, st));
+  // cell classes over the flattened (k, j, i) cells (the solver's policy rule)
+  TRY3(launch_prepare(env->obstacle, env->target, m->cls, grid->nx, m->ny, grid->nt, m->delta, subgrid_L, st));
+  ++launches;
+
+  ba.nx = grid->nx; ba.ny = grid->ny; ba.nz = grid->nz; ba.nt = grid->nt; ba.K = env->K; ba.N = N; ba.A = A;
+  ba.A_pad = A_pad; ba.spw = m->spw; ba.L = subgrid_L; ba.h = h; ba.row_cap = row_cap;
+  ba.Nc = m->Nc; ba.nS = m->nS; ba.n_slices = m->n_slices; ba.rows_pad = m->rows_pad;
+  ba.lam = (float)lam; ba.dx = grid->dx; ba.dt = grid->dt;
+  ba.vbar = env->vbar; ba.modes = env->modes; ba.Y = Y; ba.gbar = env->gbar;
+  ba.cls = m->cls; ba.target = env->target; ba.obstacle = env->obstacle;
+  ba.rw = rw;
+  ba.slice_off = m->slice_off; ba.slice_w = m->slice_w; ba.nnz = m->nnz; ba.sinkc = m->sinkc;
+  ba.R = m->R; ba.cnt = m->cnt;
+  // shared memory: the L^3 window plus the staged velocities of one chunk
+  const size_t win = (size_t)m->nbins * 128;
+  const size_t per_item = 3 * fsz;
+  int chunk = (int)std::min<size_t>((size_t)N, (64 * 1024) / (per_item * m->spw));
+  chunk = std::max(chunk, 1);
+  ba.chunk = chunk;
+  const size_t smem = win + (size_t)chunk * m->spw * per_item;
+  const void *kfn = prec == MDP_FP64_CHECK ? (const void *)build3d_kernel<double> : (const void *)build3d_kernel<float>;
+  TRY3(allow_max_smem(kfn));
+  int per_sm = 0;
+  TRY3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
+  if (per_sm < 1) {
+    release();
+    set_error("the 3-D window does not fit shared memory (reduce subgrid_L)");
+    return fail(MDP_ERR_ARG);
+  }
+  const int64_t blocks = std::min<int64_t>((int64_t)num_sms() * per_sm, m->n_slices);
+  unsigned long long c[CNT_N];
+  for (int attempt = 0;; ++attempt) {
+    ba.pool = m->pool;
+    ba.pool_cap_cols = cap_cols;
+    if (prec == MDP_FP64_CHECK)
+      build3d_kernel<double><<<(unsigned)blocks, 256, smem, st>>>(ba);
+    else
+      build3d_kernel<float><<<(unsigned)blocks, 256, smem, st>>>(ba);
+    TRY3(cudaGetLastError());
+    ++launches;
+    TRY3(cudaMemcpyAsync(c, m->cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    TRY3(cudaStreamSynchronize(st));
+    const uint64_t worst = cols_for(row_cap);
+    if (c[CNT_POOL_FULL] == 0 || attempt > 0 || worst <= cap_cols) break;
+    dev_free(m->pool, st);
+    cap_cols = worst;
+    TRY3(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+    TRY3(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_CAPPED, st));
+    TRY3(cudaMemsetAsync(m->cnt + CNT_WORK, 0, sizeof(unsigned long long) * (CNT_N - CNT_WORK), st));
+  }
+  release();
+  cudaEventRecord(ev1, st);
+  cudaEventSynchronize(ev1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (c[CNT_OVERFLOW]) {
+    set_error(std::to_string(c[CNT_OVERFLOW]) + " landing(s) left the neighbouring 3-D sub-grid; use a larger subgrid_L");
+    return fail(MDP_ERR_SUBGRID_OVERFLOW);
+  }
+  if (c[CNT_ROW_CAP]) {
+    set_error("a row had more successors than the row cap");
+    return fail(MDP_ERR_ELL_OVERFLOW);
+  }
+  if (c[CNT_POOL_FULL]) {
+    set_error("entry pool capacity exhausted (device memory budget)");
+    return fail(MDP_ERR_OOM);
+  }
+  m->pool_cols = c[CNT_POOL_COLS];
+  m->nnz_total = (int64_t)c[CNT_NNZ];
+  m->nnz_domain = (int64_t)c[CNT_DOMAIN];
+  m->max_row_nnz = (int32_t)c[CNT_MAXROW];
+  m->samples = (int64_t)c[CNT_SAMPLES];
+  if (m->pool_cols < cap_cols) {   // compaction: the bump-allocated columns are contiguous
+    uint32_t *np = nullptr;
+    TRY3(dev_alloc((void **)&np, (size_t)std::max<uint64_t>(m->pool_cols, 1) * 128, st));
+    if (m->pool_cols) TRY3(cudaMemcpyAsync(np, m->pool, (size_t)m->pool_cols * 128, cudaMemcpyDeviceToDevice, st));
+    dev_free(m->pool, st);
+    m->pool = np;
+    cap_cols = std::max<uint64_t>(m->pool_cols, 1);
+  }
+  m->build_ms = ms;
+  m->kernel_ms = ms;
+  m->launches = launches;
+  m->device_bytes = (int64_t)cap_cols * 128 + 5 * m->n_slices + 3 * m->rows_pad +
+                    (int64_t)fsz * m->rows_pad * n_obj + m->nS + 8 * CNT_N;
+  *out = m;
+#undef TRY3
+  return MDP_OK;
+}

@@ -64,6 +64,22 @@ class MdpSolveStats(C.Structure):
                 ("backups", C.c_int64)]
 
 
+class MdpGrid3D(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nt", C.c_int32),
+                ("dx", C.c_double), ("dt", C.c_double)]
+
+
+class MdpEnv3D(C.Structure):
+    _fields_ = [("K", C.c_int32), ("precision", C.c_int32), ("vbar", P), ("modes", P), ("coeffs", P),
+                ("sigma_h", P), ("seed", C.c_uint64), ("mdp_id", C.c_uint64), ("gbar", P),
+                ("obstacle", P), ("target", P)]
+
+
+class MdpActions3D(C.Structure):
+    _fields_ = [("A", C.c_int32), ("table_h", P), ("c_f", C.c_double), ("c_r", C.c_double),
+                ("r_term", C.c_double), ("r_outbound", C.c_double)]
+
+
 class MdpRolloutSummary(C.Structure):
     _fields_ = [("mean_return", C.c_double * 3), ("p_target", C.c_double),
                 ("mean_steps_target", C.c_double), ("paths", C.c_int64)]
@@ -97,6 +113,7 @@ SIGNATURES = {
     "mdp_model_free": (None, [P]),
     "mdp_solve_multi": (C.c_int, [P, C.c_int32, P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_solve_noalloc": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
+    "mdp_build3d": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, P, P]),
     "mdp_rollout": (C.c_int, [P, P, P, C.c_int32, P, P, C.c_int32, P, C.c_int32, P, P, P, P, P]),
     "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
                                     C.c_int32, P, P]),
@@ -202,6 +219,49 @@ class DeviceEnv:
         return a
 
 
+class DeviceEnv3D:
+    """Device copies (torch tensors) of an inputs.Environment3D in one precision."""
+
+    def __init__(self, env, precision: int = MDP_FP32, device="cuda"):
+        import torch
+        ft = torch.float64 if precision == MDP_FP64_CHECK else torch.float32
+        self.env, self.precision = env, precision
+        self.vbar = torch.as_tensor(np.ascontiguousarray(env.vbar)).to(device, ft).contiguous()
+        self.modes = torch.as_tensor(np.ascontiguousarray(env.modes)).to(device, ft).contiguous()
+        self.gbar = (torch.as_tensor(np.ascontiguousarray(env.gbar)).to(device, ft).contiguous()
+                     if env.gbar is not None else None)
+        self.obstacle = torch.as_tensor(np.ascontiguousarray(env.obstacle, dtype=np.uint8)).to(device)
+        self.target = torch.as_tensor(np.ascontiguousarray(env.target, dtype=np.uint8)).to(device)
+        self.coeffs = None
+        if env.Y is not None:
+            self.coeffs = torch.as_tensor(np.ascontiguousarray(env.Y)).to(device, ft).contiguous()
+        self.sigma = np.ascontiguousarray(env.sigma, dtype=np.float64)
+        self.table = np.ascontiguousarray(env.actions, dtype=np.float64)
+
+    def c_env(self) -> MdpEnv3D:
+        e = MdpEnv3D()
+        e.K, e.precision = self.env.K, self.precision
+        e.vbar, e.modes, e.coeffs = _ptr(self.vbar), _ptr(self.modes), _ptr(self.coeffs)
+        e.sigma_h = self.sigma.ctypes.data_as(P).value
+        e.seed, e.mdp_id = int(self.env.seed), int(self.env.mdp_id)
+        e.gbar = _ptr(self.gbar)
+        e.obstacle, e.target = _ptr(self.obstacle), _ptr(self.target)
+        return e
+
+    def c_grid(self) -> MdpGrid3D:
+        g = MdpGrid3D()
+        g.nx, g.ny, g.nz, g.nt = self.env.nx, self.env.ny, self.env.nz, self.env.nt
+        g.dx, g.dt = self.env.dx, self.env.dt
+        return g
+
+    def c_actions(self) -> MdpActions3D:
+        a = MdpActions3D()
+        a.A = self.env.A
+        a.table_h = self.table.ctypes.data_as(P).value
+        a.c_f, a.c_r, a.r_term, a.r_outbound = self.env.c_f, self.env.c_r, self.env.r_term, self.env.r_outbound
+        return a
+
+
 class Model:
     """Owner of an mdp_model handle."""
 
@@ -237,6 +297,19 @@ def mdp_build(denv: DeviceEnv, N: Optional[int] = None, subgrid_L: Optional[int]
     code = lib.mdp_build(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
                          C.byref(opts) if opts is not None else None, _stream(stream), C.byref(h))
     _check(code, "mdp_build")
+    return Model(h.value, denv.precision)
+
+
+def mdp_build3d(denv: DeviceEnv3D, objs: Sequence[int] = (MDP_OBJ_TIME,), N: Optional[int] = None,
+                subgrid_L: Optional[int] = None, stream=None) -> Model:
+    """The build on a 3-D grid; the model works with mdp_solve / mdp_export_csr."""
+    e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    h = P()
+    N = denv.env.N if N is None else N
+    L = denv.env.L if subgrid_L is None else subgrid_L
+    _check(load().mdp_build3d(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
+                              _stream(stream), C.byref(h)), "mdp_build3d")
     return Model(h.value, denv.precision)
 
 
