@@ -157,24 +157,30 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    env = workload(args.config)
     import oracle
+    if args.config == "cube":
+        from paper_2109_00857_gb300 import inputs
+        env = inputs.cube(with_gbar=True, objectives=(0, 1, 2), name="cube-64x64x16x40-N1000-A24-3obj")
+        build = lambda a, b: oracle.build3d_units(env, env.objectives, a, b)
+    else:
+        env = workload(args.config)
+        build = lambda a, b: oracle.build_units(env, env.objectives, a, b, with_literal=False)
     Y = oracle.coeffs_for(env)
     env.Y = Y
     t_mid = env.nt // 2
     u0 = t_mid * env.Nc
     per_unit = env.N * env.A
     t0 = time.perf_counter()
-    oracle.build_units(env, env.objectives, u0, u0 + 2, with_literal=False)
+    build(u0, u0 + 2)
     per = (time.perf_counter() - t0) / 2
     n = max(2, int(args.ref_step_seconds / max(per, 1e-6)))
     for w in range(args.warmup):
-        oracle.build_units(env, env.objectives, u0, u0 + n, with_literal=False)
+        build(u0, u0 + n)
     times = []
     for k in range(args.steps):
         a = u0 + (k * n) % max(1, env.Nc - n)
         t0 = time.perf_counter()
-        oracle.build_units(env, env.objectives, a, a + n, with_literal=False)
+        build(a, a + n)
         times.append(time.perf_counter() - t0)
     T = sum(times)
     val = args.steps * n * per_unit / T
@@ -252,6 +258,93 @@ def run_batch(args):
             "speedup_vs_sequential": plain_s / batch_s, "sweeps_max": max(sweeps)}
     print(json.dumps(line), flush=True)
     b.close()
+
+
+def run_cube(args):
+    """The 3-D grid (Sec. II-A with n = 3): one step = the 3-D build of all
+    three objectives + one fused Jacobi solve, inputs resident in HBM."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import inputs, mdp
+    mdp.load()
+    env = inputs.cube(with_gbar=True, objectives=(0, 1, 2), name="cube-64x64x16x40-N1000-A24-3obj")
+    objs = env.objectives
+    denv = mdp.DeviceEnv3D(env, mdp.MDP_FP32)
+    stream = torch.cuda.Stream()
+    Vbuf = [torch.empty(env.nS + 1, dtype=torch.float32, device="cuda") for _ in objs]
+    Pbuf = [torch.empty(env.nS, dtype=torch.int16, device="cuda") for _ in objs]
+    rec = {}
+
+    def step():
+        m = mdp.mdp_build3d(denv, objs=objs, stream=stream)
+        info = m.info()
+        _, _, sts = mdp.mdp_solve_multi(m, tuple(range(len(objs))), tol=0.0, V=Vbuf, policy=Pbuf,
+                                        stream=stream)
+        rec["info"], rec["stats"] = info, sts
+        m.free()
+        return info, sts
+
+    for _ in range(args.warmup):
+        step()
+    clk = ClockSampler(0)
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms, build_ms, solve_ms, samples, backups, launches, full_equiv = [], [], [], 0, 0, 0, 0.0
+    e0.record(stream)
+    for _ in range(args.steps):
+        info, sts = step()
+        kern_ms.append(info.kernel_ms)
+        build_ms.append(info.build_ms)
+        solve_ms.append(sts[0].solve_ms)
+        samples += info.samples
+        backups += sum(s.backups for s in sts)
+        full_equiv += max(s.backups / (env.nS * env.A) for s in sts)
+        launches += info.launches + (env.nt + 1) + len(sts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_ms = e0.elapsed_time(e1)
+    info = rec["info"]
+    hbm, sm_mhz, peak_kind = peaks()
+    bpsw = bellman_bytes_per_sweep(info, env.nS, len(objs))
+    sweep_ms = sum(solve_ms) / max(full_equiv, 1e-9)
+    bell = bpsw / (sweep_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": samples / (t_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": env.name, "grid": [env.nx, env.ny, env.nz, env.nt], "K": env.K,
+                       "N": env.N, "A": env.A, "subgrid": f"{env.L}^3", "objectives": list(objs),
+                       "solve": "jacobi (fused objectives)", "tol": 0.0, "l2": "inputs_gt_l2"},
+            "build_transitions_per_s": info.samples / (statistics.mean(build_ms) / 1e3),
+            "bellman_updates_per_s": backups / (sum(solve_ms) / 1e3),
+            "phase_ms": {"build": statistics.mean(build_ms), "build_kernel": statistics.mean(kern_ms),
+                         "solve": statistics.mean(solve_ms)},
+            "sweeps": [s.sweeps for s in rec["stats"]],
+            "roofline_bellman": {"kernel": "bellman_kernel", "bound": "hbm", "achieved": bell, "peak": hbm,
+                                 "unit": "GB/s", "frac": bell / hbm, "bytes_per_sweep": bpsw,
+                                 "ms_per_sweep": sweep_ms, "peak_basis": f"hbm_gbs ({peak_kind})"},
+            "gpu_launches": launches, "clocks": clocks,
+            "model": {"nnz": info.nnz, "rows": info.rows, "max_row_nnz": info.max_row_nnz,
+                      "device_bytes": info.device_bytes}}
+    if not args.no_cpu_baseline:
+        import oracle
+        env.Y = oracle.coeffs_for(env)
+        s0 = (env.nt // 2) * env.Nc + env.Nc // 3
+        t0 = time.perf_counter()
+        oracle.build3d_units(env, objs, s0, s0 + 2)
+        per = max(time.perf_counter() - t0, 1e-6) / 2
+        n = max(2, min(env.Nc, int(args.cpu_seconds / per)))
+        t0 = time.perf_counter()
+        out = oracle.build3d_units(env, objs, s0, s0 + n)
+        dt = time.perf_counter() - t0
+        assert out["status"] == 0
+        line["cpu_baseline"] = {"value": n * env.N * env.A / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} start states of layer t={env.nt // 2} x {env.A} actions x "
+                                          f"N={env.N}, FP64 3-D oracle build, 1 thread, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
 
 
 def run_serve(args):
@@ -369,7 +462,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve"])
+    ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve", "cube"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", default="20,50,100,200,400")
     ap.add_argument("--solve", default="jacobi", choices=["jacobi", "jacobi_full", "layered"])
@@ -392,6 +485,9 @@ def main():
         return
     if args.config == "serve":
         run_serve(args)
+        return
+    if args.config == "cube":
+        run_cube(args)
         return
 
     import torch

@@ -313,9 +313,28 @@ def rollout(env, policy, start, objs=(OBJ_TIME,), with_traj=False):
 
 
 # ---------------------------------------------------------------- 3-D grid --
-def build3d(env, objs=(OBJ_TIME,), max_nnz=None) -> OracleModel:
-    """The 3-D build (inputs.Environment3D), reordered into the paper layout
-    row = a*|S| + s."""
+def build3d_units(env, objs, s_begin, s_end, max_nnz=None):
+    """Run the 3-D oracle build over start states [s_begin, s_end) (s = t*Nc + c).
+    Returns the raw local-row arrays (nnz, col, cnt, R, overflow, status)."""
+    p, keep = _problem3d(env)
+    A = env.A
+    if max_nnz is None:
+        max_nnz = env.L ** 3 + 1
+    rows = (s_end - s_begin) * A
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    nnz = np.zeros(rows, dtype=np.int32)
+    col = np.zeros(rows * max_nnz, dtype=np.int64)
+    cnt = np.zeros(rows * max_nnz, dtype=np.int32)
+    R = np.zeros(len(ob) * rows, dtype=np.float64)
+    ovf = C.c_int64(0)
+    st = lib().orc_build3d(C.byref(p), s_begin, s_end, max_nnz, _p(ob), len(ob), _p(nnz), _p(col),
+                           _p(cnt), _p(R), C.byref(ovf))
+    return dict(nnz=nnz, col=col.reshape(rows, max_nnz), cnt=cnt.reshape(rows, max_nnz),
+                R=R.reshape(len(ob), rows), overflow=ovf.value, status=st)
+
+
+def _problem3d(env):
+    """The ctypes Problem3D of an inputs.Environment3D and the arrays it points into."""
     keep = []
 
     def hold(a, dt):
@@ -338,6 +357,13 @@ def build3d(env, objs=(OBJ_TIME,), max_nnz=None) -> OracleModel:
     p.target = _p(hold(env.target, np.uint8))
     p.act = _p(hold(env.actions, np.float64))
     p.c_f, p.c_r, p.r_term, p.r_outbound = env.c_f, env.c_r, env.r_term, env.r_outbound
+    return p, keep
+
+
+def build3d(env, objs=(OBJ_TIME,), max_nnz=None) -> OracleModel:
+    """The 3-D build (inputs.Environment3D), reordered into the paper layout
+    row = a*|S| + s."""
+    p, keep = _problem3d(env)
     nS, A = env.nS, env.A
     if max_nnz is None:
         max_nnz = env.L ** 3 + 1

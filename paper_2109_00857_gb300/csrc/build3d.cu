@@ -11,7 +11,9 @@
 // the staged realizations into a full L^3 window hist[bin][l] with a
 // shared-memory reduction (phase B: a lane only touches its own bank); warp 0
 // turns each row's window into ascending entries with the sink folded and
-// R(s,a) from the counts.  FP32 lands with the exact floor of u + d per axis
+// R(s,a) from the counts.  The landing offsets are monotone in the velocity,
+// so the offsets of a state's smallest and largest u per axis bound every
+// landing of a row: the emit scans that box instead of all L^3 bins.  FP32 lands with the exact floor of u + d per axis
 // (the 2-D path's landing offsets); FP64 check mode evaluates the oracle's
 // literal formulas in its order without contraction.
 #include <algorithm>
@@ -57,13 +59,32 @@ struct U3 {
   RT x, y, z;
 };
 
+// Offset bound of one axis for the emit box: the landing offset of u clamped
+// to [-h-1, h+1] (monotone in u like the landing itself).
+__device__ __forceinline__ int box_offset(float u, int c, float th, int h) {
+  const float n = floorf(u);
+  const float f = n + (float)c + ((u - n) >= th ? 1.f : 0.f);
+  return (int)fminf(fmaxf(f, (float)(-h - 1)), (float)(h + 1));
+}
+
+__device__ __forceinline__ int box_offset64(double v, double d, int64_t i, double dx, double dt, int h) {
+  const double x = __dmul_rn((double)i + 0.5, dx);
+  const double xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, d), dt));
+  const double f = floor(__ddiv_rn(xp, dx)) - (double)i;
+  if (f >= (double)(-h - 1) && f <= (double)(h + 1)) return (int)f;
+  return f < 0.0 ? -h - 1 : h + 1;
+}
+
 template <typename RT>
-__global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
+__global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(Build3Args a) {
   extern __shared__ __align__(16) unsigned char smem3[];
   const int nb = a.L * a.L * a.L;
   uint32_t *hist = reinterpret_cast<uint32_t *>(smem3);   // [nb][32]
   U3<RT> *ubuf = reinterpret_cast<U3<RT> *>(smem3 + (size_t)nb * 128);   // [chunk][spw]
+  RT *sbox = reinterpret_cast<RT *>(smem3 + (size_t)nb * 128 +
+                                    (((size_t)a.chunk * a.spw * sizeof(U3<RT>) + 15) & ~(size_t)15));   // [warp][spw][6]
   __shared__ long long s_slice;
+  unsigned long long loc_tot = 0, loc_dom = 0, loc_samp = 0, loc_max = 0;   // warp 0 lane 0
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int h = a.h, L = a.L;
   const int64_t Nc = a.Nc, nxy = (int64_t)a.nx * a.ny;
@@ -91,6 +112,7 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
     int kind_l = act_ok ? kind(s_l) : KIND_NONE;
     const int kind_t = kind(s_t);
     const int any = __syncthreads_or(kind_t == KIND_SAMPLE);
+    RT mn[3] = {(RT)INFINITY, (RT)INFINITY, (RT)INFINITY}, mx[3] = {-(RT)INFINITY, -(RT)INFINITY, -(RT)INFINITY};
     if (any) {
       const int64_t t = s_t / Nc, c = s_t % Nc;
       const RT *Yt = Yall + (size_t)t * a.N * a.K;
@@ -128,6 +150,8 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
             u.z = vz;
           }
           ubuf[(size_t)w * a.spw + q_t] = u;
+          mn[0] = fmin(mn[0], u.x); mn[1] = fmin(mn[1], u.y); mn[2] = fmin(mn[2], u.z);
+          mx[0] = fmax(mx[0], u.x); mx[1] = fmax(mx[1], u.y); mx[2] = fmax(mx[2], u.z);
         }
         __syncthreads();
         // ---- phase B: lane l bins row l's landings of the staged realizations
@@ -166,8 +190,24 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
         }
         __syncthreads();
       }
+      // the extreme u of each state: lanes of equal q_t are lane + multiples of spw
+      for (int off = 16; off >= a.spw; off >>= 1) {
+        for (int x = 0; x < 3; ++x) {
+          mn[x] = fmin(mn[x], __shfl_xor_sync(0xffffffffu, mn[x], off));
+          mx[x] = fmax(mx[x], __shfl_xor_sync(0xffffffffu, mx[x], off));
+        }
+      }
+      if (lane < a.spw) {
+        RT *sb = sbox + ((size_t)warp * a.spw + lane) * 6;
+        for (int x = 0; x < 3; ++x) {
+          sb[x] = mn[x];
+          sb[3 + x] = mx[x];
+        }
+      }
+      __syncthreads();
     }
-    // ---- emit (warp 0): ascending bins (dk, dj, di), sink folded, R from counts
+    // ---- emit (warp 0): ascending bins (dk, dj, di) of the row's box, sink
+    // folded, R from counts
     if (warp == 0) {
       const int64_t ir = sl * 32 + lane;
       const int64_t t = s_l / Nc, c = s_l % Nc;
@@ -175,15 +215,39 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
       const int64_t nxt = (t + 1) * Nc;
       int e = 0;
       uint32_t sink = 0;
+      int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
       if (kind_l == KIND_SAMPLE) {
-        for (int b = 0; b < nb; ++b) {
-          const uint32_t n = hist[b * 32 + lane];
-          if (!n) continue;
-          const int64_t ip = li + (b % L) - h, jp = lj + (b / L) % L - h, kp = lk + b / (L * L) - h;
-          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
-          if (!inside || a.obstacle[nxt + (kp * a.ny + jp) * a.nx + ip]) sink += n;
-          else ++e;
+        RT umn[3] = {(RT)INFINITY, (RT)INFINITY, (RT)INFINITY}, umx[3] = {-(RT)INFINITY, -(RT)INFINITY, -(RT)INFINITY};
+        for (int w = 0; w < nwarps; ++w) {
+          const RT *sb = sbox + ((size_t)w * a.spw + q_l) * 6;
+          for (int x = 0; x < 3; ++x) {
+            umn[x] = fmin(umn[x], sb[x]);
+            umx[x] = fmax(umx[x], sb[3 + x]);
+          }
         }
+        const int64_t pos[3] = {li, lj, lk};
+        for (int x = 0; x < 3; ++x) {
+          if constexpr (sizeof(RT) == 4) {
+            lo[x] = box_offset(umn[x], a.act.c[x][a_l], a.act.th[x][a_l], h);
+            hi[x] = box_offset(umx[x], a.act.c[x][a_l], a.act.th[x][a_l], h);
+          } else {
+            lo[x] = box_offset64(umn[x], a.act.d64[x][a_l], pos[x], a.dx, a.dt, h);
+            hi[x] = box_offset64(umx[x], a.act.d64[x][a_l], pos[x], a.dx, a.dt, h);
+          }
+          lo[x] = max(lo[x], -h);
+          hi[x] = min(hi[x], h);
+        }
+        for (int dk = lo[2]; dk <= hi[2]; ++dk)
+          for (int dj = lo[1]; dj <= hi[1]; ++dj)
+            for (int di = lo[0]; di <= hi[0]; ++di) {
+              const int b = ((dk + h) * L + (dj + h)) * L + (di + h);
+              const uint32_t n = hist[b * 32 + lane];
+              if (!n) continue;
+              const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
+              const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+              if (!inside || a.obstacle[nxt + (kp * a.ny + jp) * a.nx + ip]) sink += n;
+              else ++e;
+            }
       } else if (kind_l == KIND_SINK) {
         sink = (uint32_t)a.N;
       }
@@ -206,29 +270,30 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
       if (kind_l == KIND_SAMPLE) {
         const RT F = sizeof(RT) == 4 ? (RT)a.act.F[a_l] : (RT)a.act.F64[a_l];
         const RT g_s = a.gbar ? static_cast<const RT *>(a.gbar)[s_l] : (RT)0;
-        for (int b = 0; b < nb; ++b) {
-          uint32_t *hp = hist + b * 32 + lane;
-          const uint32_t n = *hp;
-          if (!n) continue;
-          *hp = 0;
-          const int di = b % L - h, dj = (b / L) % L - h, dk = b / (L * L) - h;
-          const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
-          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
-          const int64_t cp = (kp * a.ny + jp) * a.nx + ip;
-          if (!inside || a.obstacle[nxt + cp]) continue;
-          if (write) dst[(size_t)k * 32] = entry_word((int)(dk * nxy + dj * a.nx + di), n);
-          ++k;
-          const bool is_t = a.target[cp] != 0;
-          const RT g_sp = a.gbar ? static_cast<const RT *>(a.gbar)[nxt + cp] : (RT)0;
-          for (int o = 0; o < a.rw.n_obj; ++o) {
-            if constexpr (sizeof(RT) == 4) {
-              Racc[o] = fmaf((float)n / (float)a.N, step_reward32(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t), Racc[o]);
-            } else {
-              const double p = __ddiv_rn((double)n, (double)a.N);
-              Racc[o] = __dadd_rn(Racc[o], __dmul_rn(p, step_reward64(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t)));
+        for (int dk = lo[2]; dk <= hi[2]; ++dk)
+          for (int dj = lo[1]; dj <= hi[1]; ++dj)
+            for (int di = lo[0]; di <= hi[0]; ++di) {
+              uint32_t *hp = hist + (((dk + h) * L + (dj + h)) * L + (di + h)) * 32 + lane;
+              const uint32_t n = *hp;
+              if (!n) continue;
+              *hp = 0;
+              const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
+              const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+              const int64_t cp = (kp * a.ny + jp) * a.nx + ip;
+              if (!inside || a.obstacle[nxt + cp]) continue;
+              if (write) dst[(size_t)k * 32] = entry_word((int)(dk * nxy + dj * a.nx + di), n);
+              ++k;
+              const bool is_t = a.target[cp] != 0;
+              const RT g_sp = a.gbar ? static_cast<const RT *>(a.gbar)[nxt + cp] : (RT)0;
+              for (int o = 0; o < a.rw.n_obj; ++o) {
+                if constexpr (sizeof(RT) == 4) {
+                  Racc[o] = fmaf((float)n / (float)a.N, step_reward32(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t), Racc[o]);
+                } else {
+                  const double p = __ddiv_rn((double)n, (double)a.N);
+                  Racc[o] = __dadd_rn(Racc[o], __dmul_rn(p, step_reward64(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t)));
+                }
+              }
             }
-          }
-        }
         if (sink) {
           for (int o = 0; o < a.rw.n_obj; ++o) {
             if constexpr (sizeof(RT) == 4)
@@ -261,14 +326,18 @@ __global__ void __launch_bounds__(256) build3d_kernel(Build3Args a) {
         dom += __shfl_xor_sync(0xffffffffu, dom, off);
       }
       const int sampled = __popc(__ballot_sync(0xffffffffu, kind_l == KIND_SAMPLE));
-      if (lane == 0) {
-        atomicAdd(&a.cnt[CNT_NNZ], (unsigned long long)tot);
-        atomicAdd(&a.cnt[CNT_DOMAIN], (unsigned long long)dom);
-        atomicAdd(&a.cnt[CNT_SAMPLES], (unsigned long long)sampled * (unsigned long long)a.N);
-        atomicMax(&a.cnt[CNT_MAXROW], (unsigned long long)W);
-      }
+      loc_tot += (unsigned long long)tot;
+      loc_dom += (unsigned long long)dom;
+      loc_samp += (unsigned long long)sampled * (unsigned long long)a.N;
+      loc_max = max(loc_max, (unsigned long long)W);
     }
     __syncthreads();
+  }
+  if (tid == 0) {
+    atomicAdd(&a.cnt[CNT_NNZ], loc_tot);
+    atomicAdd(&a.cnt[CNT_DOMAIN], loc_dom);
+    atomicAdd(&a.cnt[CNT_SAMPLES], loc_samp);
+    atomicMax(&a.cnt[CNT_MAXROW], loc_max);
   }
 }
 
@@ -442,7 +511,7 @@ extern "C" mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, 
   int chunk = (int)std::min<size_t>((size_t)N, (64 * 1024) / (per_item * m->spw));
   chunk = std::max(chunk, 1);
   ba.chunk = chunk;
-  const size_t smem = win + (size_t)chunk * m->spw * per_item;
+  const size_t smem = win + (((size_t)chunk * m->spw * per_item + 15) & ~(size_t)15) + (size_t)8 * m->spw * 6 * fsz;
   const void *kfn = prec == MDP_FP64_CHECK ? (const void *)build3d_kernel<double> : (const void *)build3d_kernel<float>;
   TRY3(allow_max_smem(kfn));
   int per_sm = 0;
