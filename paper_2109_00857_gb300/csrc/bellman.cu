@@ -150,6 +150,7 @@ struct PipeRange {
   int64_t s_lo, s_hi;     // states whose V this launch writes
   int stage_bytes;        // bytes per stage
   int dtab_smem;          // 1: delta table staged in shared memory
+  int grouped;            // 1: bellman_kernel_g (kGS states per warp step)
 };
 
 // one stage holds a slice's entry columns (at most wcap of them)
@@ -434,6 +435,270 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_kernel(SolveArgs a, VS
   bellman_body<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
 }
 
+// ---- grouped sweep: kGS states per warp step (models with A_pad = 32) ----
+// One slice per state (A_pad = 32) makes the per-slice epilogue of
+// bellman_body (a max/argmax over 32 lanes per objective, the stage refill,
+// the writes) cost as much as the slice's backups.  Here a warp takes kGS
+// consecutive slices at a time: lane (q, g) owns state q of the group and the
+// actions g, g + kGL, g + 2 kGL, ... (ascending), forms their Q values one
+// after another in registers and keeps the running maximum (strict >, so the
+// lowest action wins ties); a log2(kGL)-step shuffle reduction over the kGL
+// lanes of each state finishes the max/argmax.  Each row is still summed by
+// one lane in ascending column order, so values and policy equal
+// bellman_body's bit for bit.  The kGS slices of a group are copied into
+// fixed slots of one stage (slot = wcap columns + 32 bytes: the 8-bank skew
+// between slots keeps the lanes' shared-memory reads conflict-free).
+constexpr int kGS = 4;           // states (slices) per group
+constexpr int kGL = 32 / kGS;    // lanes per state
+constexpr int kWarpsG = 16;      // warps per CTA: one CTA per SM (one V(s') window per L1)
+
+static int slot_bytes_g(int wcap) { return wcap * 128 + 32; }
+
+template <typename RT, int NO>
+__device__ __forceinline__ void bellman_body_g(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
+                                               int64_t b_hi, const PipeRange &pr, unsigned char *sm,
+                                               double *wmax, int *wst_s) {
+  unsigned live = (1u << NO) - 1u;
+  if (k > 1) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (v.res[o] && __longlong_as_double((long long)v.res[o][k - 2]) <= a.tol) live &= ~(1u << o);
+  }
+  if (!live) return;
+  if (*(volatile int *)a.err) return;   // an earlier launch of this solve timed out
+  if (a.work && k >= 1 && blockIdx.x == 0 && threadIdx.x == 0) a.work[k - 1] = (unsigned long long)(pr.sl_hi - pr.sl_lo);
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // [kWarpsG][kDepth]
+  unsigned char *ring = sm + 256;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n_local = b_hi - b_lo;
+  if (n_local <= 0) return;
+
+  if (tid < kWarpsG * kDepth) mbar_init(smem_u32(full + tid), 1);
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  const int slot = pr.stage_bytes / kGS;
+  unsigned char *myring = ring + (size_t)warp * kDepth * pr.stage_bytes;
+  const int n_groups = (int)((n_local + kGS - 1) / kGS);
+  const int n_mine = (n_groups > warp) ? (n_groups - warp + kWarpsG - 1) / kWarpsG : 0;
+  const int first0 = (int)b_lo + warp * kGS;      // first slice of my j-th group: first0 + j*gstep
+  const int gstep = kWarpsG * kGS;
+  const int hi = (int)b_hi;
+  const uint32_t ring0 = smem_u32(myring), bar0 = smem_u32(full + warp * kDepth);
+  const uint64_t stream_policy = l2_evict_first();
+  const int q = lane / kGL, g = lane % kGL;
+
+  // lane l: metadata of slice l % kGS of my group 32/kGS * (j / (32/kGS)) + l / kGS
+  constexpr int kMetaG = 32 / kGS;
+  uint32_t m_off = 0, m_w = 0;
+  // issue(j, st): lanes 0..kGS-1 copy the slices of my j-th group into their
+  // slots of stage st (whole warp calls it)
+  auto issue = [&](int j, int st) {
+    if (j % kMetaG == 0) {   // one coalesced load for the next kMetaG groups
+      const int sl = first0 + (j + lane / kGS) * gstep + lane % kGS;
+      m_off = 0;
+      m_w = 0;
+      if (sl < hi) {
+        m_off = __ldg(a.slice_off + sl);
+        m_w = __ldg(a.slice_w + sl);
+      }
+    }
+    const int src = (j % kMetaG) * kGS + (lane % kGS);
+    const uint32_t off = __shfl_sync(0xffffffffu, m_off, src);
+    uint32_t W = __shfl_sync(0xffffffffu, m_w, src);
+    if (lane >= kGS) W = 0;
+    uint32_t tot = W;
+#pragma unroll
+    for (int m = 1; m < kGS; m <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, m);
+    const uint32_t fb = bar0 + 8u * (uint32_t)st;
+    if (lane < kGS) wst_s[(warp * kDepth + st) * kGS + lane] = (int)W;
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage
+      mbar_expect_tx(fb, tot * 128u);
+    }
+    __syncwarp();
+    if (lane < kGS && W) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_g2s_stream(ring0 + (uint32_t)(st * pr.stage_bytes + lane * slot), a.pool + (size_t)off * 32, W * 128u,
+                      fb, stream_policy);
+    }
+    __syncwarp();
+  };
+  // R of my j-th group (lane (q, g): rows g + i*kGL of slice q) and, on the
+  // head lanes, the state's current values and class: loaded one group ahead
+  auto load_r = [&](int j, RT (&Rr)[kGS][NO], VPack<RT, NO> &old, uint8_t &cls) {
+    const int sl = first0 + j * gstep + q;
+    if (sl < hi) {
+#pragma unroll
+      for (int i = 0; i < kGS; ++i)
+#pragma unroll
+        for (int o = 0; o < NO; ++o) Rr[i][o] = __ldcs(v.R[o] + (size_t)sl * 32 + i * kGL + g);
+      if (g == 0) {
+        old = v.in[sl];
+        cls = __ldg(a.cls + sl);
+      }
+    }
+  };
+
+  const int nS = (int)a.nS, Nc = (int)a.Nc;
+  const int s_lo = (int)pr.s_lo, s_hi = (int)pr.s_hi;
+  const RT invN = (RT)1 / (RT)a.N;
+  float rf[NO];
+  double r[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    rf[o] = 0.f;
+    r[o] = 0.0;
+  }
+  for (int j = 0; j < kDepth && j < n_mine; ++j) issue(j, j);
+  RT Rn[kGS][NO];
+#pragma unroll
+  for (int i = 0; i < kGS; ++i)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) Rn[i][o] = (RT)0;
+  VPack<RT, NO> old_n{};
+  uint8_t cls_n = 0;
+  if (n_mine > 0) load_r(0, Rn, old_n, cls_n);
+  int st = 0;
+  uint32_t phase = 0;
+  int s = first0 + q;   // spw = 1: state = slice
+  uint8_t *chg_out = a.lflags ? a.lflags + (size_t)(k % 3) * (a.nt + 1) : nullptr;
+  int t_cur = s / Nc, t_end = (t_cur + 1) * Nc;
+  bool chg = false;
+  for (int j = 0; j < n_mine; ++j, s += gstep) {
+    if (!mbar_wait(bar0 + 8u * (uint32_t)st, phase)) {
+      if (lane == 0) atomicOr(a.err, 1);
+      for (int jj = j + 1; jj < j + kDepth && jj < n_mine; ++jj)
+        mbar_wait(bar0 + 8u * (uint32_t)(jj % kDepth), (uint32_t)(jj / kDepth) & 1);
+      break;
+    }
+    const uint32_t *ent = reinterpret_cast<const uint32_t *>(myring + st * pr.stage_bytes + q * slot) + g;
+    const int Wq = wst_s[(warp * kDepth + st) * kGS + q];
+    RT Rv[kGS][NO];
+#pragma unroll
+    for (int i = 0; i < kGS; ++i)
+#pragma unroll
+      for (int o = 0; o < NO; ++o) Rv[i][o] = Rn[i][o];
+    const VPack<RT, NO> old = old_n;
+    const uint8_t cls_s = cls_n;
+    if (j + 1 < n_mine) load_r(j + 1, Rn, old_n, cls_n);
+    const bool in_rng = s < hi && s >= s_lo && s < s_hi;
+    const int sn = (s + Nc <= nS) ? s + Nc : nS;
+    const VPack<RT, NO> *Vn = v.in + sn;
+    Acc<RT> acc[kGS][NO];
+#pragma unroll(NO == 1 ? 4 : 1)
+    for (int kk = 0; kk < Wq; ++kk) {   // every column of the slice, ascending
+#pragma unroll
+      for (int i = 0; i < kGS; ++i) {
+        const uint32_t w = ent[kk * 32 + i * kGL];
+        const VPack<RT, NO> gv = Vn[(int)(int16_t)(w & 0xFFFFu)];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) acc[i][o].add(w >> 16, gv.v[o], a.N);
+      }
+    }
+    __syncwarp();
+    if (j + kDepth < n_mine) issue(j + kDepth, st);   // refill the stage just read
+    if (++st == kDepth) {
+      st = 0;
+      phase ^= 1u;
+    }
+    // running max over my actions (ascending, strict >: the lowest wins ties)
+    RT qv[NO];
+    int qa[NO];
+    // (states outside the range are not written, so only padding actions
+    // need masking)
+    const bool full_a = a.A == 32;
+#pragma unroll
+    for (int i = 0; i < kGS; ++i) {
+      const int act = i * kGL + g;
+      const bool valid = full_a || act < a.A;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const RT x = valid ? acc[i][o].q(Rv[i][o], invN) : -(RT)INFINITY;
+        if (i == 0 || x > qv[o]) {
+          qv[o] = x;
+          qa[o] = act;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+#pragma unroll
+      for (int m = 1; m < kGL; m <<= 1) {
+        const RT oq = __shfl_xor_sync(0xffffffffu, qv[o], m);
+        const int oa = __shfl_xor_sync(0xffffffffu, qa[o], m);
+        if (oq > qv[o] || (oq == qv[o] && oa < qa[o])) {
+          qv[o] = oq;
+          qa[o] = oa;
+        }
+      }
+    }
+    const bool head = g == 0 && in_rng;   // the lane that writes state s
+    const bool term = head && cls_s != CLS_FREE;
+    VPack<RT, NO> nv;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const bool upd = (live >> o) & 1u;
+      nv.v[o] = upd ? qv[o] : old.v[o];
+      if (head && upd) {
+        v.pol[o][s] = term ? (int16_t)-1 : (int16_t)qa[o];
+        if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv[o] - old.v[o]));
+        else r[o] = fmax(r[o], fabs(qv[o] - old.v[o]));
+      }
+    }
+#pragma unroll
+    for (int o = NO; o < VPack<RT, NO>::W; ++o) nv.v[o] = (RT)0;
+    if (head) {
+      v.out[s] = nv;
+      if (chg_out) {
+        if (s >= t_end) {
+          if (chg) chg_out[t_cur] = 1;
+          chg = false;
+          do { ++t_cur; t_end += Nc; } while (s >= t_end);
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          if constexpr (sizeof(RT) == 4) chg |= __float_as_uint(nv.v[o]) != __float_as_uint(old.v[o]);
+          else chg |= __double_as_longlong(nv.v[o]) != __double_as_longlong(old.v[o]);
+        }
+      }
+    }
+  }
+  if (chg_out && chg) chg_out[t_cur] = 1;
+  if (v.res[0]) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      double ro = (sizeof(RT) == 4) ? (double)rf[o] : r[o];
+      for (int m = 16; m > 0; m >>= 1) ro = fmax(ro, __shfl_xor_sync(0xffffffffu, ro, m));
+      if (lane == 0) wmax[warp * NO + o] = ro;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      if (tid == o) {
+        double m = 0.0;
+        for (int i = 0; i < kWarpsG; ++i) m = fmax(m, wmax[i * NO + o]);
+        if (m > 0.0) atomicMax(&v.res[o][k - 1], (unsigned long long)__double_as_longlong(m));
+      }
+    }
+  }
+}
+
+template <typename RT, int NO>
+__global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_kernel_g(SolveArgs a, VSet<RT, NO> v,
+                                                                                       int k, PipeRange pr) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWarpsG * NO];
+  __shared__ int wst_s[kWarpsG * kDepth * kGS];   // columns of each slot of each stage
+  if (a.lflags && k >= 1 && !active_range(a, k, pr, blockIdx.x == 0)) return;
+  // CTA ranges in whole groups so that a group never straddles two CTAs
+  const int64_t total = pr.sl_hi - pr.sl_lo;
+  const int64_t groups = (total + kGS - 1) / kGS;
+  const int64_t per_cta = (groups + gridDim.x - 1) / gridDim.x * kGS;
+  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
+  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
+  bellman_body_g<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
+}
+
 // Plan of batched Jacobi sweep k (one block): per model, the slices of the
 // layers whose inputs changed in sweep k-1 (nothing once the model met the
 // tolerance or ran max_sweeps), with the model's flags for sweep k+1
@@ -519,6 +784,7 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   pr.s_hi = it.a.nS;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
+  pr.grouped = 0;
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
   v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
@@ -594,8 +860,27 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
 
 template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
-  pr->stage_bytes = stage_bytes_for(a.wcap);
   pr->dtab_smem = 0;
+  // grouped sweep for one state per slice while a group's stage stays small
+  // (kWarpsG warps x kDepth stages fit shared memory up to 16 columns)
+  pr->grouped = (a.spw == 1 && a.wcap <= 16) ? 1 : 0;
+  if (pr->grouped) {
+    pr->stage_bytes = kGS * slot_bytes_g(a.wcap);
+    *smem = 256 + (size_t)kWarpsG * kDepth * pr->stage_bytes;
+    cudaError_t e = allow_max_smem((const void *)bellman_kernel_g<RT, NO>);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel_g<RT, NO>, 32 * kWarpsG, *smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t b = (int64_t)num_sms() * per_sm;
+    const int64_t want = (slices + 2 * kGS * kWarpsG - 1) / (2 * kGS * kWarpsG);   // >= 2 groups per warp
+    if (b > want) b = want;
+    if (b < 1) b = 1;
+    *blocks = (int)b;
+    return cudaSuccess;
+  }
+  pr->stage_bytes = stage_bytes_for(a.wcap);
   *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
   if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = allow_max_smem((const void *)bellman_kernel<RT, NO>);
@@ -652,6 +937,15 @@ __global__ void finalize_multi_kernel(const double *stats_base, size_t blk, int 
   }
 }
 
+template <typename RT, int NO>
+static void launch_sweep(const SolveArgs &a, const VSet<RT, NO> &v, int k, const PipeRange &pr, int blocks,
+                         size_t smem, cudaStream_t st) {
+  if (pr.grouped)
+    bellman_kernel_g<RT, NO><<<blocks, 32 * kWarpsG, smem, st>>>(a, v, k, pr);
+  else
+    bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, k, pr);
+}
+
 // Objective o's status block: stats_d + o*(4 + max_sweeps) holds sweeps,
 // residual, (objective 0: the error word), spare, then one residual slot
 // per sweep.  NO = 1 iterates in the caller's V and io.Vtmp[0]; NO > 1 in
@@ -692,7 +986,7 @@ static cudaError_t jacobi_t(const SolveArgs &a, int max_sweeps, const SolveIO &i
   pr.s_lo = 0;
   pr.s_hi = a.nS;
   for (int k = 1; k <= max_sweeps; ++k)
-    bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, (k & 1) ? odd : even, k, pr);
+    launch_sweep<RT, NO>(a, (k & 1) ? odd : even, k, pr, blocks, smem, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t fb = (a.nS + 1 + 255) / 256;
@@ -763,7 +1057,7 @@ static cudaError_t layered_t(const SolveArgs &a, int nt, const SolveIO &io, doub
     pr.s_hi = pr.s_lo + a.Nc;
     pr.sl_lo = pr.s_lo / a.spw;
     pr.sl_hi = (pr.s_hi + a.spw - 1) / a.spw;
-    bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, 0, pr);
+    launch_sweep<RT, NO>(a, v, 0, pr, blocks, smem, st);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || NO == 1) return e;
