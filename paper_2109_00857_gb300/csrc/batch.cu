@@ -42,6 +42,8 @@ struct Item {
   int max_sweeps = 0;
   int L = 0;
   int64_t pool_cols = 0;
+  int width = 1;       // widest slice (columns), from the calibration build
+  int solve_cls = 0;   // 1: grouped sweep
 };
 
 }  // namespace
@@ -53,9 +55,15 @@ struct mdp_batch_t {
   BuildArgs *items_d = nullptr;
   int64_t *prefix_d = nullptr;
   unsigned long long *work_d = nullptr;
-  BatchSolveItem *sitems_d = nullptr;
-  BatchCta *ctas_d = nullptr;
-  int n_ctas = 0, cap_bins = 2048, kmax = 0, stage_bytes = 0, max_sweeps_all = 0, cta_threads = 256;
+  BatchSolveItem *sitems_d = nullptr;   // [n]: the warp-per-slice class first, then the grouped class
+  int cap_bins = 2048, kmax = 0, max_sweeps_all = 0, cta_threads = 256;
+  // solve classes: 0 = warp-per-slice sweep, 1 = grouped sweep (one state
+  // per slice, narrow enough); each with its own plan entries
+  struct SolveClass {
+    int first = 0, n = 0, wcap = 1, stage_bytes = 0, n_ctas = 0;
+    BatchCta *ctas_d = nullptr;
+  };
+  SolveClass cls[2];
   // build launches: items grouped by (states per warp, mode count), each
   // group one persistent launch over its own zero-based prefix segment
   struct Group {
@@ -92,7 +100,7 @@ void batch_release(mdp_batch_t *b) {
   dev_free(b->prefix_d, b->st);
   dev_free(b->work_d, b->st);
   dev_free(b->sitems_d, b->st);
-  dev_free(b->ctas_d, b->st);
+  for (auto &c : b->cls) dev_free(c.ctas_d, b->st);
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->cnt_h) cudaFreeHost(b->cnt_h);
   if (b->stats_h) cudaFreeHost(b->stats_h);
@@ -135,8 +143,13 @@ cudaError_t enqueue(mdp_batch_t *b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags, 1, (size_t)nt, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags + nt, 0, 2 * (size_t)nt + 3, st);
   }
-  for (int k = 1; k <= b->max_sweeps_all && e == cudaSuccess; ++k)
-    e = launch_bellman_batch(b->sitems_d, b->n, b->ctas_d, b->n_ctas, k, b->stage_bytes, st);
+  for (int k = 1; k <= b->max_sweeps_all && e == cudaSuccess; ++k) {
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+      const auto &C = b->cls[c];
+      if (C.n > 0)
+        e = launch_bellman_batch(b->sitems_d + C.first, C.n, C.ctas_d, C.n_ctas, k, C.stage_bytes, c, st);
+    }
+  }
   if (e == cudaSuccess) e = launch_finalize_batch(b->sitems_d, b->n, st);
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
     Item &it = b->items[i];
@@ -178,7 +191,6 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   b->items.resize(n);
   // ---- calibration (autotuner): one plain build per item
   int64_t total_slices = 0, wide = 0;
-  int wcap = 1;
   for (int i = 0; i < n; ++i) {
     Item &it = b->items[i];
     it.desc = items_h[i];
@@ -208,7 +220,8 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     }
     it.L = cm->L;
     it.pool_cols = (int64_t)cm->pool_cols;
-    wcap = std::max(wcap, cm->max_row_nnz);
+    it.width = std::max(1, cm->max_row_nnz);
+    it.solve_cls = bellman_grouped_fits(cm->spw, it.width) ? 1 : 0;
     wide += cm->deferred;
     total_slices += cm->n_slices;
     b->kmax = std::max(b->kmax, it.desc.env.K);
@@ -222,9 +235,30 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   std::vector<int64_t> prefix(n + 1, 0);
   std::vector<BatchSolveItem> sitems(n);
 
-  int per_sm = 1;
-  cudaError_t ce = prepare_bellman_batch(wcap, &b->stage_bytes, &per_sm);
-  if (ce != cudaSuccess) return fail(cuda_fail(ce, "prepare_bellman_batch"));
+  // solve classes: the warp-per-slice items first, then the grouped ones
+  // (the same item order within each), each with its own widest slice
+  std::vector<int> slot(n);
+  for (int c = 0, pos = 0; c < 2; ++c) {
+    auto &C = b->cls[c];
+    C.first = pos;
+    for (int i = 0; i < n; ++i) {
+      if (b->items[i].solve_cls != c) continue;
+      slot[i] = pos++;
+      C.wcap = std::max(C.wcap, b->items[i].width);
+    }
+    C.n = pos - C.first;
+  }
+  cudaError_t ce = cudaSuccess;
+  for (int c = 0; c < 2; ++c) {
+    auto &C = b->cls[c];
+    if (C.n == 0) continue;
+    int per_sm = 1;
+    ce = prepare_bellman_batch(C.wcap, c, &C.stage_bytes, &per_sm);
+    if (ce != cudaSuccess) return fail(cuda_fail(ce, "prepare_bellman_batch"));
+    // two waves of CTAs share each sweep's recomputed slices (plus one entry
+    // per model for the chunk remainders)
+    C.n_ctas = num_sms() * std::max(per_sm, 1) * 2;
+  }
   for (int i = 0; i < n; ++i) {
     Item &it = b->items[i];
     mdp_build_opts o{};
@@ -252,10 +286,10 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     args[i].defer_in = it.hook.defer;
     b->cta_smem = std::max(b->cta_smem, fp32_smem_bytes(args[i], b->cta_threads));
     prefix[i + 1] = prefix[i] + m->n_slices;
-    BatchSolveItem &si = sitems[i];
+    BatchSolveItem &si = sitems[slot[i]];
     memset(&si, 0, sizeof(si));
     si.a.pool = m->pool; si.a.slice_off = m->slice_off; si.a.slice_w = m->slice_w; si.a.nnz = m->nnz;
-    si.a.wcap = wcap;
+    si.a.wcap = b->cls[it.solve_cls].wcap;
     si.a.err = reinterpret_cast<int *>(it.stats + 2);
     si.a.R = m->R; si.a.cls = m->cls; si.a.delta = m->delta;
     si.a.nS = m->nS; si.a.Nc = m->Nc; si.a.n_slices = m->n_slices;
@@ -271,9 +305,6 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     si.stats = it.stats;
     si.max_sweeps = it.max_sweeps;
   }
-  // sweep grid: two waves of CTAs share each sweep's recomputed slices (plus
-  // one entry per model for the chunk remainders)
-  b->n_ctas = num_sms() * std::max(per_sm, 1) * 2;
   // group the build items by (states per warp, mode count); prefix segments per group
   std::vector<int> ord(n);
   for (int i = 0; i < n; ++i) ord[i] = i;
@@ -304,7 +335,8 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->prefix_d, sizeof(int64_t) * gprefix.size(), b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->work_d, sizeof(unsigned long long) * b->groups.size(), b->st);
   if (ce == cudaSuccess) ce = dev_alloc((void **)&b->sitems_d, sizeof(BatchSolveItem) * n, b->st);
-  if (ce == cudaSuccess) ce = dev_alloc((void **)&b->ctas_d, sizeof(BatchCta) * (b->n_ctas + n), b->st);
+  for (auto &C : b->cls)
+    if (ce == cudaSuccess && C.n > 0) ce = dev_alloc((void **)&C.ctas_d, sizeof(BatchCta) * (C.n_ctas + C.n), b->st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(b->items_d, sorted.data(), sizeof(BuildArgs) * n, cudaMemcpyHostToDevice, b->st);
   if (ce == cudaSuccess)

@@ -453,6 +453,10 @@ constexpr int kGL = 32 / kGS;    // lanes per state
 constexpr int kWarpsG = 16;      // warps per CTA: one CTA per SM (one V(s') window per L1)
 
 static int slot_bytes_g(int wcap) { return wcap * 128 + 32; }
+static size_t grouped_smem(int wcap) { return 256 + (size_t)kWarpsG * kDepth * kGS * slot_bytes_g(wcap); }
+// dynamic shared memory the grouped kernel may take: the opt-in maximum per
+// CTA (227 KB) less its static arrays and a margin
+constexpr size_t kGroupedSmemMax = 227 * 1024 - 2048;
 
 template <typename RT, int NO>
 __device__ __forceinline__ void bellman_body_g(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
@@ -794,6 +798,33 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   bellman_body<float, 1>(it.a, v, k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
 }
 
+// The same over models with one state per slice, by the grouped sweep.
+__global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_batch_kernel_g(const BatchSolveItem *items,
+                                                                       const BatchCta *ctas, int k,
+                                                                       int stage_bytes) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWarpsG];
+  __shared__ int wst_s[kWarpsG * kDepth * kGS];
+  const BatchCta c = ctas[blockIdx.x];
+  if (c.item < 0) return;
+  const BatchSolveItem &it = items[c.item];
+  PipeRange pr;
+  pr.sl_lo = c.sl_lo;
+  pr.sl_hi = c.sl_hi;
+  pr.s_lo = 0;
+  pr.s_hi = it.a.nS;
+  pr.stage_bytes = stage_bytes;
+  pr.dtab_smem = 0;
+  pr.grouped = 1;
+  VSet<float, 1> v;
+  v.R[0] = static_cast<const float *>(it.a.R);
+  v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
+  v.out = reinterpret_cast<VPack<float, 1> *>((k & 1) ? it.Vb : it.Va);
+  v.pol[0] = it.policy;
+  v.res[0] = it.res;
+  bellman_body_g<float, 1>(it.a, v, k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
+}
+
 // Per model (one block each): sweeps and residual, final iterate into Va.
 __global__ void finalize_batch_kernel(const BatchSolveItem *items) {
   const BatchSolveItem &it = items[blockIdx.x];
@@ -812,13 +843,18 @@ __global__ void finalize_batch_kernel(const BatchSolveItem *items) {
 }
 
 cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
-                                 int stage_bytes, cudaStream_t st) {
+                                 int stage_bytes, int grouped, cudaStream_t st) {
   if (n > 1023) return cudaErrorInvalidValue;
   plan_batch_kernel<<<1, 1024, 0, st>>>(items_d, n, k, ctas_d, G, G + n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = 256 + (size_t)kWarps * kDepth * stage_bytes;
-  bellman_batch_kernel<<<G + n, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+  if (grouped) {
+    const size_t smem = 256 + (size_t)kWarpsG * kDepth * stage_bytes;
+    bellman_batch_kernel_g<<<G + n, 32 * kWarpsG, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+  } else {
+    const size_t smem = 256 + (size_t)kWarps * kDepth * stage_bytes;
+    bellman_batch_kernel<<<G + n, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+  }
   return cudaGetLastError();
 }
 
@@ -827,7 +863,17 @@ cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm) {
+bool bellman_grouped_fits(int spw, int wcap) { return spw == 1 && grouped_smem(wcap) <= kGroupedSmemMax; }
+
+cudaError_t prepare_bellman_batch(int wcap, int grouped, int *stage_bytes, int *per_sm) {
+  if (grouped) {
+    *stage_bytes = kGS * slot_bytes_g(wcap);
+    const size_t smem = grouped_smem(wcap);
+    if (smem > kGroupedSmemMax) return cudaErrorInvalidConfiguration;
+    cudaError_t e = allow_max_smem((const void *)bellman_batch_kernel_g);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bellman_batch_kernel_g, 32 * kWarpsG, smem);
+  }
   *stage_bytes = stage_bytes_for(wcap);
   const size_t smem = 256 + (size_t)kWarps * kDepth * (*stage_bytes);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -861,12 +907,13 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
 template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
   pr->dtab_smem = 0;
-  // grouped sweep for one state per slice while a group's stage stays small
-  // (kWarpsG warps x kDepth stages fit shared memory up to 16 columns)
-  pr->grouped = (a.spw == 1 && a.wcap <= 16) ? 1 : 0;
+  // grouped sweep for one state per slice while kWarpsG warps x kDepth
+  // stages of kGS slots fit one CTA's shared memory (slices up to 13
+  // columns); wider models take the warp-per-slice kernel
+  pr->grouped = (a.spw == 1 && grouped_smem(a.wcap) <= kGroupedSmemMax) ? 1 : 0;
   if (pr->grouped) {
     pr->stage_bytes = kGS * slot_bytes_g(a.wcap);
-    *smem = 256 + (size_t)kWarpsG * kDepth * pr->stage_bytes;
+    *smem = grouped_smem(a.wcap);
     cudaError_t e = allow_max_smem((const void *)bellman_kernel_g<RT, NO>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

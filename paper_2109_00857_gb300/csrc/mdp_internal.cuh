@@ -215,11 +215,14 @@ struct BatchCta {
   int item;
   int64_t sl_lo, sl_hi;
 };
-cudaError_t prepare_bellman_batch(int wcap, int *stage_bytes, int *per_sm);
+// grouped: models with one state per slice whose width fits the grouped
+// sweep (bellman_grouped_fits); else the warp-per-slice sweep
+bool bellman_grouped_fits(int spw, int wcap);
+cudaError_t prepare_bellman_batch(int wcap, int grouped, int *stage_bytes, int *per_sm);
 // sweep k: a plan launch spreads the models' recomputed slices over G + n
 // CTA entries (ctas_d), then the sweep launch; n <= 1023 models
 cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
-                                 int stage_bytes, cudaStream_t st);
+                                 int stage_bytes, int grouped, cudaStream_t st);
 cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st);
 // batched build (FP32): one persistent warp launch over the slices of n
 // models that share the mode count K and the states per warp spw (prefix[m]

@@ -375,3 +375,30 @@ def test_zero_flow_values_are_chebyshev_distance_on_gpu(mdp):
                 d = min(max(abs(i - a), abs(j - b)) for a, b in zip(ti, tj))
                 if 0 < d <= nt - 1 - t:
                     assert V[t * nx * ny + j * nx + i] == pytest.approx(3.0 - d, abs=1e-5)
+
+
+@pytest.mark.parametrize("scale,width", [(1.2, 12), (1.4, 14), (1.6, 16)])
+def test_solvers_on_both_sides_of_the_grouped_sweep_width(mdp, scale, width):
+    """32 actions with the widest slice at 12, 14 and 16 columns: the grouped
+    sweep (four states per warp step, up to 13 columns) and the warp-per-slice
+    sweep above it both return the oracle's values and policy in check mode,
+    fused and single-objective, Jacobi and layered; FP32 passes the solver
+    gate on its own exported model."""
+    env = inputs.energy(nx=18, ny=16, nt=5, N=800, L=15, objectives=(0, 1, 2),
+                        sigma=tuple(scale * x for x in (0.3, 0.2, 0.15, 0.1)))
+    ref = oracle.build(env, objs=(0, 1, 2))
+    fx = oracle.fixed_mask(env)
+    model = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP64_CHECK), objs=(0, 1, 2))
+    assert model.info().max_row_nnz == width
+    for meth in (mdp.MDP_SOLVE_JACOBI, mdp.MDP_SOLVE_LAYERED):
+        Vs, pis, sts = mdp.mdp_solve_multi(model, (0, 1, 2), method=meth, tol=0.0)
+        for o in range(3):
+            Vo, pio, sw, res = oracle.vi_jacobi(ref, ref.R[o], fx, tol=0.0, nt=env.nt)
+            np.testing.assert_allclose(Vs[o].cpu().numpy(), Vo, rtol=1e-12, atol=1e-12)
+            assert np.array_equal(pis[o].cpu().numpy(), pio)
+            V1, pi1, st1 = mdp.mdp_solve(model, o, method=meth, tol=0.0)
+            assert np.array_equal(V1.cpu().numpy().view(np.uint64), Vs[o].cpu().numpy().view(np.uint64))
+            assert np.array_equal(pi1.cpu().numpy(), pis[o].cpu().numpy())
+    m32 = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), objs=(0, 1, 2))
+    for o in range(3):
+        solver_parity(mdp, env, m32, o)
