@@ -318,8 +318,12 @@ mdp_status mdp_rollout(const mdp_env *env, const mdp_grid *grid, const mdp_actio
  * recomputed layers evenly over the GPU; all captured in a CUDA graph that is
  * replayed on each call with the same shapes.  Arrays are host arrays of
  * per-MDP descriptors; V[i] / policy[i] are device outputs as in mdp_solve
- * (FP32 only).  Objective slot 0 of each MDP is solved with (active-layer)
- * Jacobi to tol; results equal mdp_build + mdp_solve of each MDP alone. */
+ * (FP32 only).  Objective slot 0 of each MDP is solved to tol: tol > 0 by
+ * (active-layer) Jacobi sweeps, tol = 0 by the layered pass (one batched step
+ * per time layer, every model's layer nt - k at step k; the exact fixed
+ * point, equal to Jacobi's bit for bit; sweeps_h reports 1 as mdp_solve's
+ * layered method does).  V and policy equal mdp_build + mdp_solve of each
+ * MDP alone. */
 typedef struct {
   mdp_env env;
   mdp_grid grid;

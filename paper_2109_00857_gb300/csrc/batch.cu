@@ -56,7 +56,10 @@ struct mdp_batch_t {
   int64_t *prefix_d = nullptr;
   unsigned long long *work_d = nullptr;
   BatchSolveItem *sitems_d = nullptr;   // [n]: the warp-per-slice class first, then the grouped class
-  int cap_bins = 2048, kmax = 0, max_sweeps_all = 0, cta_threads = 256;
+  int cap_bins = 2048, kmax = 0, max_sweeps_all = 0, max_nt = 0, cta_threads = 256;
+  // tol = 0: the exact fixed point by one layered pass per model (Jacobi's
+  // result bit for bit, one step per time layer); tol > 0: Jacobi sweeps
+  bool layered = false;
   // solve classes: 0 = warp-per-slice sweep, 1 = grouped sweep (one state
   // per slice, narrow enough); each with its own plan entries
   struct SolveClass {
@@ -143,14 +146,16 @@ cudaError_t enqueue(mdp_batch_t *b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags, 1, (size_t)nt, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(it.lflags + nt, 0, 2 * (size_t)nt + 3, st);
   }
-  for (int k = 1; k <= b->max_sweeps_all && e == cudaSuccess; ++k) {
+  const int steps = b->layered ? b->max_nt : b->max_sweeps_all;
+  for (int k = 1; k <= steps && e == cudaSuccess; ++k) {
     for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
       const auto &C = b->cls[c];
       if (C.n > 0)
-        e = launch_bellman_batch(b->sitems_d + C.first, C.n, C.ctas_d, C.n_ctas, k, C.stage_bytes, c, st);
+        e = launch_bellman_batch(b->sitems_d + C.first, C.n, C.ctas_d, C.n_ctas, k, C.stage_bytes, c,
+                                 b->layered ? 1 : 0, st);
     }
   }
-  if (e == cudaSuccess) e = launch_finalize_batch(b->sitems_d, b->n, st);
+  if (e == cudaSuccess) e = launch_finalize_batch(b->sitems_d, b->n, b->layered ? 1 : 0, st);
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
     Item &it = b->items[i];
     e = cudaMemcpyAsync(b->cnt_h + (size_t)i * CNT_N, it.m->cnt, sizeof(unsigned long long) * CNT_N,
@@ -183,6 +188,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
   cudaGetDevice(&b->device);
   b->n = n;
   b->tol = tol;
+  b->layered = (tol == 0.0);
   cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
   auto fail = [&](mdp_status code) {
     batch_release(b);
@@ -275,6 +281,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     it.m = m;
     it.max_sweeps = m->nt + 1;
     b->max_sweeps_all = std::max(b->max_sweeps_all, it.max_sweeps);
+    b->max_nt = std::max(b->max_nt, m->nt);
     b->cta_threads = it.hook.threads;
     const size_t vbytes = sizeof(float) * (size_t)(m->nS + 1);
     ce = dev_alloc((void **)&it.Vb, vbytes, b->st);
@@ -296,7 +303,7 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     si.a.A = m->A; si.a.A_pad = m->A_pad; si.a.spw = m->spw; si.a.N = m->N; si.a.nbins = m->nbins;
     si.a.tol = tol;
     si.a.nt = m->nt;
-    si.a.lflags = it.lflags;
+    si.a.lflags = b->layered ? nullptr : it.lflags;
     si.a.work = nullptr;
     si.Va = static_cast<float *>(it.desc.V);
     si.Vb = it.Vb;

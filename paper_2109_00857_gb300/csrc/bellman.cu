@@ -706,20 +706,31 @@ __global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_kernel_g(SolveArgs a,
 // Plan of batched Jacobi sweep k (one block): per model, the slices of the
 // layers whose inputs changed in sweep k-1 (nothing once the model met the
 // tolerance or ran max_sweeps), with the model's flags for sweep k+1
-// cleared; then the total is cut into chunks of about total / G slices,
+// cleared; layered (tol = 0): the slices of layer nt - k of every model that
+// has it.  Then the total is cut into chunks of about total / G slices,
 // each model's range into whole chunks, so every CTA entry of the sweep
 // holds one model's contiguous range (entries past the last: item -1).
 // n <= blockDim.x.
 __global__ void plan_batch_kernel(const BatchSolveItem *items, int n, int k, BatchCta *ctas, int G,
-                                  int n_entries) {
+                                  int n_entries, int layered) {
   __shared__ long long s_cnt[1024];
   __shared__ int s_ctas[1024];
   __shared__ long long s_chunk;
   const int i = threadIdx.x;
-  long long lo = 0, hi = 0;
-  if (i < n) {
+  long long lo = 0, hi = 0, s_lo = 0, s_hi = 0;
+  if (i < n && layered) {   // step k: layer nt - k of every model that has it
+    const SolveArgs &a = items[i].a;
+    const int t = a.nt - k;
+    if (t >= 0 && !*(volatile int *)a.err) {
+      s_lo = (long long)t * a.Nc;
+      s_hi = s_lo + a.Nc;
+      lo = s_lo / a.spw;
+      hi = min((long long)a.n_slices, (s_hi + a.spw - 1) / a.spw);
+    }
+  } else if (i < n) {
     const BatchSolveItem &it = items[i];
     const SolveArgs &a = it.a;
+    s_hi = a.nS;
     const bool done = k > it.max_sweeps ||
                       (k > 1 && __longlong_as_double((long long)it.res[k - 2]) <= a.tol) ||
                       *(volatile int *)a.err;
@@ -759,13 +770,13 @@ __global__ void plan_batch_kernel(const BatchSolveItem *items, int n, int k, Bat
     for (int j = 0; j < i; ++j) first += s_ctas[j];
     for (int c = 0; c < s_ctas[i] && first + c < n_entries; ++c) {
       const long long a0 = lo + (long long)c * chunk;
-      ctas[first + c] = BatchCta{i, a0, min(hi, a0 + chunk)};
+      ctas[first + c] = BatchCta{i, a0, min(hi, a0 + chunk), s_lo, s_hi};
     }
   }
   if (i == n) {   // unused entries
     int used = 0;
     for (int j = 0; j < n; ++j) used += s_ctas[j];
-    for (int e = used; e < n_entries; ++e) ctas[e] = BatchCta{-1, 0, 0};
+    for (int e = used; e < n_entries; ++e) ctas[e] = BatchCta{-1, 0, 0, 0, 0};
   }
 }
 
@@ -774,7 +785,7 @@ __global__ void plan_batch_kernel(const BatchSolveItem *items, int n, int k, Bat
 // own residual.
 __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const BatchSolveItem *items,
                                                                     const BatchCta *ctas, int k,
-                                                                    int stage_bytes) {
+                                                                    int stage_bytes, int layered) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double wmax[kWarps];
   __shared__ int wst_s[kWarps * kDepth];
@@ -784,24 +795,25 @@ __global__ void __launch_bounds__(32 * kWarps, 4) bellman_batch_kernel(const Bat
   PipeRange pr;
   pr.sl_lo = c.sl_lo;
   pr.sl_hi = c.sl_hi;
-  pr.s_lo = 0;
-  pr.s_hi = it.a.nS;
+  pr.s_lo = c.s_lo;
+  pr.s_hi = c.s_hi;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
   pr.grouped = 0;
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
-  v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
-  v.out = reinterpret_cast<VPack<float, 1> *>((k & 1) ? it.Vb : it.Va);
+  // Jacobi: ping-pong (sweep k reads Va when k is odd); layered: in place in Va
+  v.in = reinterpret_cast<const VPack<float, 1> *>((layered || (k & 1)) ? it.Va : it.Vb);
+  v.out = reinterpret_cast<VPack<float, 1> *>((layered || !(k & 1)) ? it.Va : it.Vb);
   v.pol[0] = it.policy;
-  v.res[0] = it.res;
-  bellman_body<float, 1>(it.a, v, k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
+  v.res[0] = layered ? nullptr : it.res;
+  bellman_body<float, 1>(it.a, v, layered ? 0 : k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
 }
 
 // The same over models with one state per slice, by the grouped sweep.
 __global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_batch_kernel_g(const BatchSolveItem *items,
                                                                        const BatchCta *ctas, int k,
-                                                                       int stage_bytes) {
+                                                                       int stage_bytes, int layered) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double wmax[kWarpsG];
   __shared__ int wst_s[kWarpsG * kDepth * kGS];
@@ -811,24 +823,32 @@ __global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_batch_kernel_g(const 
   PipeRange pr;
   pr.sl_lo = c.sl_lo;
   pr.sl_hi = c.sl_hi;
-  pr.s_lo = 0;
-  pr.s_hi = it.a.nS;
+  pr.s_lo = c.s_lo;
+  pr.s_hi = c.s_hi;
   pr.stage_bytes = stage_bytes;
   pr.dtab_smem = 0;
   pr.grouped = 1;
   VSet<float, 1> v;
   v.R[0] = static_cast<const float *>(it.a.R);
-  v.in = reinterpret_cast<const VPack<float, 1> *>((k & 1) ? it.Va : it.Vb);
-  v.out = reinterpret_cast<VPack<float, 1> *>((k & 1) ? it.Vb : it.Va);
+  // Jacobi: ping-pong (sweep k reads Va when k is odd); layered: in place in Va
+  v.in = reinterpret_cast<const VPack<float, 1> *>((layered || (k & 1)) ? it.Va : it.Vb);
+  v.out = reinterpret_cast<VPack<float, 1> *>((layered || !(k & 1)) ? it.Va : it.Vb);
   v.pol[0] = it.policy;
-  v.res[0] = it.res;
-  bellman_body_g<float, 1>(it.a, v, k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
+  v.res[0] = layered ? nullptr : it.res;
+  bellman_body_g<float, 1>(it.a, v, layered ? 0 : k, pr.sl_lo, pr.sl_hi, pr, sm, wmax, wst_s);
 }
 
 // Per model (one block each): sweeps and residual, final iterate into Va.
-__global__ void finalize_batch_kernel(const BatchSolveItem *items) {
+__global__ void finalize_batch_kernel(const BatchSolveItem *items, int layered) {
   const BatchSolveItem &it = items[blockIdx.x];
   __shared__ int s_sweeps;
+  if (layered) {   // one pass, in place in Va
+    if (threadIdx.x == 0) {
+      it.stats[0] = 1.0;
+      it.stats[1] = 0.0;
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     int sw = it.max_sweeps;
     for (int k = 1; k <= it.max_sweeps; ++k)
@@ -843,23 +863,23 @@ __global__ void finalize_batch_kernel(const BatchSolveItem *items) {
 }
 
 cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
-                                 int stage_bytes, int grouped, cudaStream_t st) {
+                                 int stage_bytes, int grouped, int layered, cudaStream_t st) {
   if (n > 1023) return cudaErrorInvalidValue;
-  plan_batch_kernel<<<1, 1024, 0, st>>>(items_d, n, k, ctas_d, G, G + n);
+  plan_batch_kernel<<<1, 1024, 0, st>>>(items_d, n, k, ctas_d, G, G + n, layered);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (grouped) {
     const size_t smem = 256 + (size_t)kWarpsG * kDepth * stage_bytes;
-    bellman_batch_kernel_g<<<G + n, 32 * kWarpsG, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+    bellman_batch_kernel_g<<<G + n, 32 * kWarpsG, smem, st>>>(items_d, ctas_d, k, stage_bytes, layered);
   } else {
     const size_t smem = 256 + (size_t)kWarps * kDepth * stage_bytes;
-    bellman_batch_kernel<<<G + n, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes);
+    bellman_batch_kernel<<<G + n, 32 * kWarps, smem, st>>>(items_d, ctas_d, k, stage_bytes, layered);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st) {
-  finalize_batch_kernel<<<n, 256, 0, st>>>(items_d);
+cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, int layered, cudaStream_t st) {
+  finalize_batch_kernel<<<n, 256, 0, st>>>(items_d, layered);
   return cudaGetLastError();
 }
 

@@ -213,7 +213,8 @@ struct BatchSolveItem {
 };
 struct BatchCta {
   int item;
-  int64_t sl_lo, sl_hi;
+  int64_t sl_lo, sl_hi;   // slices of the entry
+  int64_t s_lo, s_hi;     // states it may write (layered: one layer)
 };
 // grouped: models with one state per slice whose width fits the grouped
 // sweep (bellman_grouped_fits); else the warp-per-slice sweep
@@ -221,9 +222,11 @@ bool bellman_grouped_fits(int spw, int wcap);
 cudaError_t prepare_bellman_batch(int wcap, int grouped, int *stage_bytes, int *per_sm);
 // sweep k: a plan launch spreads the models' recomputed slices over G + n
 // CTA entries (ctas_d), then the sweep launch; n <= 1023 models
+// layered: step k (1..max nt) is the in-place pass over layer nt - k of
+// every model (the exact fixed point of tol = 0, Jacobi's bit for bit)
 cudaError_t launch_bellman_batch(const BatchSolveItem *items_d, int n, BatchCta *ctas_d, int G, int k,
-                                 int stage_bytes, int grouped, cudaStream_t st);
-cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, cudaStream_t st);
+                                 int stage_bytes, int grouped, int layered, cudaStream_t st);
+cudaError_t launch_finalize_batch(const BatchSolveItem *items_d, int n, int layered, cudaStream_t st);
 // batched build (FP32): one persistent warp launch over the slices of n
 // models that share the mode count K and the states per warp spw (prefix[m]
 // = first slice of model m in the launch, prefix[n] = total); then the

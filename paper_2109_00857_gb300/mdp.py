@@ -504,9 +504,11 @@ class Server:
 
 # --------------------------------------------------------------- batching --
 class Batch:
-    """Many MDPs built and solved together (mdp_batch_*): one persistent build
-    launch, one launch per Jacobi sweep over all items, captured in a CUDA
-    graph on the first run.  Keeps the DeviceEnvs and outputs alive."""
+    """Many MDPs built and solved together (mdp_batch_*): persistent build
+    launches, then per batched step (a Jacobi sweep for tol > 0, a time layer
+    of the layered pass for tol = 0) one plan and one Bellman launch per solve
+    class over all items, captured in a CUDA graph on the first run.  Keeps
+    the DeviceEnvs and outputs alive."""
 
     def __init__(self, denvs, objectives=None, tol: float = 0.0):
         import torch

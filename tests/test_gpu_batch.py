@@ -31,8 +31,11 @@ def members():
 
 
 def test_batch_equals_members_alone_and_replays(mdp):
+    # tol = 0: the batch runs the layered pass; values and policies equal
+    # each member's solo Jacobi solve and its solo layered pass bit for bit
     envs = members()
     assert len({e.A for e in envs}) > 1 and len({e.K for e in envs}) > 1
+    assert len({e.nt for e in envs}) > 1
     denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
     b = mdp.Batch(denvs, tol=0.0)
     for rep in range(2):   # the second run replays the captured graph
@@ -40,10 +43,11 @@ def test_batch_equals_members_alone_and_replays(mdp):
         assert ms > 0
         for i, (e, d) in enumerate(zip(envs, denvs)):
             m = mdp.mdp_build(d, objs=(e.objectives[0],))
-            V, pi, st = mdp.mdp_solve(m, 0, tol=0.0)
-            assert sweeps[i] == st.sweeps, (i, sweeps[i], st.sweeps)
-            assert np.array_equal(b.V[i].cpu().numpy(), V.cpu().numpy()), i
-            assert np.array_equal(b.policy[i].cpu().numpy(), pi.cpu().numpy()), i
+            for method in (mdp.MDP_SOLVE_JACOBI, mdp.MDP_SOLVE_LAYERED):
+                V, pi, st = mdp.mdp_solve(m, 0, method=method, tol=0.0)
+                assert np.array_equal(b.V[i].cpu().numpy(), V.cpu().numpy()), (i, method)
+                assert np.array_equal(b.policy[i].cpu().numpy(), pi.cpu().numpy()), (i, method)
+            assert sweeps[i] == st.sweeps == 1, (i, sweeps[i], st.sweeps)
     b.close()
 
 
