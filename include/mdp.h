@@ -313,9 +313,10 @@ mdp_status mdp_rollout(const mdp_env *env, const mdp_grid *grid, const mdp_actio
 /* ------------------------------------------------------------- batching --
  * Builds and solves n (1..1023) independent MDPs of uneven sizes: one
  * persistent build launch per group of MDPs with the same mode count and
- * action count class over a shared work queue, and per Jacobi sweep one
+ * action count class over a shared work queue, and per batched step (a
+ * Jacobi sweep, or a time layer of the layered pass) and solve class one
  * small plan launch plus one Bellman launch that spreads every MDP's
- * recomputed layers evenly over the GPU; all captured in a CUDA graph that is
+ * recomputed slices evenly over the GPU; all captured in a CUDA graph that is
  * replayed on each call with the same shapes.  Arrays are host arrays of
  * per-MDP descriptors; V[i] / policy[i] are device outputs as in mdp_solve
  * (FP32 only).  Objective slot 0 of each MDP is solved to tol: tol > 0 by
