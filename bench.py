@@ -681,6 +681,11 @@ def main():
                   "traffic": cb["dram_bytes_per_unit"] * n_slices if cb else None,
                   "units_per_launch": n_slices,
                   "warp_inst_per_unit": cb["warp_inst_per_unit"] if cb else None,
+                  # HBM is not this kernel's bound (about 0.01 B per landing); reported as asked
+                  "dram_gbs": cb["dram_bytes_per_unit"] * n_slices / (kmean / 1e3) / 1e9 if cb else None,
+                  "dram_frac_of_hbm": cb["dram_bytes_per_unit"] * n_slices / (kmean / 1e3) / 1e9 / hbm if cb else None,
+                  "shared_atom_wavefronts_per_s": (cb.get("shared_atom_wavefronts_per_unit", 0) * n_slices /
+                                                   (kmean / 1e3)) if cb else None,
                   "counters": cb["summary"] if cb else "stale or absent: kernel changed since the capture",
                   "ms_per_launch": kmean,
                   "peak_basis": f"{sms} SMs x 4 issue slots x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
