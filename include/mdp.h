@@ -282,6 +282,23 @@ mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_a
                        int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
                        void *stream, mdp_model *out);
 
+/* FP32 counting: a slice whose realizations fit one staging chunk (N <= 5461
+ * for one state per slice), with at most 4 states per slice and at most 8
+ * distinct step thresholds per axis, counts each realization once at its
+ * fine coordinate (floor(u) - n0) S + rank(frac u) per axis and takes every
+ * (action, offset bin) count as a box sum of the fine table's prefix sums;
+ * other slices (and FP64_CHECK) count one increment per (realization,
+ * action).  Both give the same model.  per_action = 1 forces the second way
+ * for every slice (a reference for tests and comparisons). */
+typedef struct {
+  int32_t per_action;
+} mdp_build3d_opts;
+
+/* mdp_build3d with options (opts may be NULL: the defaults). */
+mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_actions3d *actions,
+                          int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                          const mdp_build3d_opts *opts, void *stream, mdp_model *out);
+
 /* ------------------------------------------------------------- rollouts --
  * Policy rollouts (Sec. IV: the optimal policy applied to every flow
  * realization from the start; the mean returns are the expected mission

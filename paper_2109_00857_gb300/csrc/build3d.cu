@@ -7,14 +7,22 @@
 // One CTA per slice (spw states x A_pad actions, 32 rows), persistent over a
 // work queue.  Per chunk of realizations the threads form the velocity of
 // their (state, realization) items once for all actions and stage it in
-// shared memory (phase A); then lane l of every warp bins row l's landings of
-// the staged realizations into a full L^3 window hist[bin][l] with a
-// shared-memory reduction (phase B: a lane only touches its own bank); warp 0
-// turns each row's window into ascending entries with the sink folded and
-// R(s,a) from the counts.  The landing offsets are monotone in the velocity,
-// so the offsets of a state's smallest and largest u per axis bound every
-// landing of a row: the emit scans that box instead of all L^3 bins.  FP32 lands with the exact floor of u + d per axis
-// (the 2-D path's landing offsets); FP64 check mode evaluates the oracle's
+// shared memory (phase A).  Counting, two ways with the same result:
+//  - per action (phase B): lane l of every warp bins row l's landings of the
+//    staged realizations into a full L^3 window hist[bin][l] (a lane only
+//    touches its own bank);
+//  - FP32 rank counting, when every realization is staged at once: as in the
+//    2-D build, the landing offset per axis is floor(u) + c + [rho >= le]
+//    with rho = #{T <= frac u} over the axis' distinct step thresholds, so
+//    one count per realization at the fine coordinate (floor(u) - n0) S + rho
+//    in a per-state 3-D table (in the window memory), an in-place 3-D prefix
+//    sum, and each (row, offset bin) count is an eight-corner box sum.
+// Warp 0 then turns each row's counts into ascending entries with the sink
+// folded and R(s,a) from the counts.  The landing offsets are monotone in the
+// velocity, so the offsets of a state's smallest and largest u per axis bound
+// every landing of a row: the emit scans that box instead of all L^3 bins.
+// FP32 lands with the exact floor of u + d per axis (the 2-D path's landing
+// offsets); FP64 check mode counts per action and evaluates the oracle's
 // literal formulas in its order without contraction.
 #include <algorithm>
 #include <cmath>
@@ -26,6 +34,8 @@
 namespace mdpgb {
 
 constexpr int kMaxL3 = 11;   // largest 3-D window side (11^3 bins x 128 B in shared memory)
+constexpr int kRank3 = 8;    // most distinct step thresholds per axis for rank counting
+constexpr int kRankSpw = 4;  // most states per slice for rank counting
 
 struct Actions3 {
   float dl[3][kMaxActions];     // displacement * dt/dx per axis (FP32 kinematics)
@@ -34,10 +44,18 @@ struct Actions3 {
   float F[kMaxActions];
   double d64[3][kMaxActions];   // displacement in FP64 (check mode)
   double F64[kMaxActions];
+  // rank counting (FP32): per axis the distinct thresholds T[0] < ... < T[D-1]
+  // (integer displacements excluded), S = D + 1 fine positions per cell and
+  // le[a] = #{T <= th[a]} (D + 1 for an integer displacement): the landing
+  // steps past floor(u) + c exactly when rho(frac u) = #{T <= frac u} >= le
+  float T[3][kRank3];
+  int32_t D[3];
+  int8_t le[3][kMaxActions];
 };
 
 struct Build3Args {
   int32_t nx, ny, nz, nt, K, N, A, A_pad, spw, L, h, row_cap, chunk;
+  int32_t rank_ok;   // FP32 rank counting allowed (thresholds and states fit)
   int64_t Nc, nS, n_slices, rows_pad;
   float lam;
   double dx, dt;
@@ -75,6 +93,26 @@ __device__ __forceinline__ int box_offset64(double v, double d, int64_t i, doubl
   return f < 0.0 ? -h - 1 : h + 1;
 }
 
+// rho(f) = #{T <= f} for f in [0, 1) (D <= kRank3 thresholds, ascending).
+__device__ __forceinline__ int rank3(float f, const float *T, int D) {
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < kRank3; ++i) r += (i < D && T[i] <= f) ? 1 : 0;
+  return r;
+}
+
+// Fine coordinate of u along one axis: (floor(u) - n0) S + rho(u - floor(u)).
+__device__ __forceinline__ int fine3(float u, int n0, int S, const float *T, int D) {
+  const float n = floorf(u);
+  return ((int)n - n0) * S + rank3(u - n, T, D);
+}
+
+// Fine table of one state (rank counting): cells [1, G] per axis after a
+// zero border, index ((x * (Gy + 1)) + y) * (Gz + 1) + z from word `base`.
+struct Geo3 {
+  int n0[3], fmin[3], G[3], base;
+};
+
 template <typename RT>
 __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(Build3Args a) {
   extern __shared__ __align__(16) unsigned char smem3[];
@@ -84,6 +122,9 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
   RT *sbox = reinterpret_cast<RT *>(smem3 + (size_t)nb * 128 +
                                     (((size_t)a.chunk * a.spw * sizeof(U3<RT>) + 15) & ~(size_t)15));   // [warp][spw][6]
   __shared__ long long s_slice;
+  __shared__ Geo3 s_geo[kRankSpw];       // rank counting: the states' fine tables
+  __shared__ long long s_cells[kRankSpw];
+  __shared__ int s_rank, s_total;        // rank counting used for this slice; table words
   unsigned long long loc_tot = 0, loc_dom = 0, loc_samp = 0, loc_max = 0;   // warp 0 lane 0
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int h = a.h, L = a.L;
@@ -97,7 +138,11 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
   for (int i = tid; i < nb * 32; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (;;) {
-    if (tid == 0) s_slice = (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+    if (tid == 0) {
+      s_slice = (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+      s_rank = 0;
+      s_total = 0;
+    }
     __syncthreads();
     const int64_t sl = s_slice;
     if (sl >= a.n_slices) break;
@@ -112,6 +157,66 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
     int kind_l = act_ok ? kind(s_l) : KIND_NONE;
     const int kind_t = kind(s_t);
     const int any = __syncthreads_or(kind_t == KIND_SAMPLE);
+    // ---- phase B: lane l bins row l's landings of the first cn staged
+    // realizations (one shared increment per realization and action)
+    auto phase_b = [&](int cn) {
+      if (kind_l == KIND_SAMPLE) {
+        const int64_t sc = s_l % Nc;
+        const int64_t li = sc % a.nx, lj = (sc / a.nx) % a.ny, lk = sc / nxy;
+        const uint32_t hb = smem_u32(hist) + (uint32_t)lane * 4u;
+        for (int w = warp; w < cn; w += nwarps) {
+          const U3<RT> u = ubuf[(size_t)w * a.spw + q_l];
+          int di, dj, dk;
+          if constexpr (sizeof(RT) == 4) {
+            di = land_offset(u.x, a.act.c[0][a_l], a.act.th[0][a_l]);
+            dj = land_offset(u.y, a.act.c[1][a_l], a.act.th[1][a_l]);
+            dk = land_offset(u.z, a.act.c[2][a_l], a.act.th[2][a_l]);
+          } else {
+            // x' = x + (v + a) dt from the cell centre, cell() = floor(x' / dx)
+            const double x = __dmul_rn((double)li + 0.5, a.dx), y = __dmul_rn((double)lj + 0.5, a.dx);
+            const double z = __dmul_rn((double)lk + 0.5, a.dx);
+            const double xp = __dadd_rn(x, __dmul_rn(__dadd_rn(u.x, a.act.d64[0][a_l]), a.dt));
+            const double yp = __dadd_rn(y, __dmul_rn(__dadd_rn(u.y, a.act.d64[1][a_l]), a.dt));
+            const double zp = __dadd_rn(z, __dmul_rn(__dadd_rn(u.z, a.act.d64[2][a_l]), a.dt));
+            const double fx = floor(__ddiv_rn(xp, a.dx)) - (double)li;
+            const double fy = floor(__ddiv_rn(yp, a.dx)) - (double)lj;
+            const double fz = floor(__ddiv_rn(zp, a.dx)) - (double)lk;
+            di = (fabs(fx) <= (double)h) ? (int)fx : h + 1;
+            dj = (fabs(fy) <= (double)h) ? (int)fy : h + 1;
+            dk = (fabs(fz) <= (double)h) ? (int)fz : h + 1;
+          }
+          if (di < -h || di > h || dj < -h || dj > h || dk < -h || dk > h) {
+            atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
+            continue;
+          }
+          const uint32_t b = (uint32_t)(((dk + h) * L + (dj + h)) * L + (di + h));
+          asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + b * 128u), "r"(1u));
+        }
+      }
+    };
+    // FP32 rank counting needs every realization staged at once
+    const bool try_rank = sizeof(RT) == 4 && a.rank_ok && a.N <= a.chunk;
+    // rank counting: the count of row (q_l, a_l)'s offset bin (di, dj, dk) is
+    // the fine table summed over X in [(di - c - n0 - 1) S + le, + S) per axis
+    // (the realizations whose landing steps to exactly that offset): eight
+    // corners of the prefix table
+    auto rank_count = [&](const Geo3 &gl, int di, int dj, int dk) -> uint32_t {
+      const int off[3] = {di, dj, dk};
+      int c0[3], c1[3];
+      for (int x = 0; x < 3; ++x) {
+        const int S = a.act.D[x] + 1;
+        const int f0 = (off[x] - a.act.c[x][a_l] - gl.n0[x] - 1) * S + a.act.le[x][a_l] - gl.fmin[x];
+        c0[x] = max(f0, 0);
+        c1[x] = min(f0 + S - 1, gl.G[x] - 1);
+        if (c0[x] > c1[x]) return 0u;
+      }
+      const int Py = gl.G[1] + 1, Pz = gl.G[2] + 1;
+      const uint32_t *P = hist + gl.base;
+      auto at = [&](int x, int y, int z) { return P[(x * Py + y) * Pz + z]; };
+      const int x0 = c0[0], y0 = c0[1], z0 = c0[2], x1 = c1[0] + 1, y1 = c1[1] + 1, z1 = c1[2] + 1;
+      return at(x1, y1, z1) - at(x0, y1, z1) - at(x1, y0, z1) - at(x1, y1, z0) + at(x0, y0, z1) +
+             at(x0, y1, z0) + at(x1, y0, z0) - at(x0, y0, z0);
+    };
     RT mn[3] = {(RT)INFINITY, (RT)INFINITY, (RT)INFINITY}, mx[3] = {-(RT)INFINITY, -(RT)INFINITY, -(RT)INFINITY};
     if (any) {
       const int64_t t = s_t / Nc, c = s_t % Nc;
@@ -154,41 +259,10 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
           mx[0] = fmax(mx[0], u.x); mx[1] = fmax(mx[1], u.y); mx[2] = fmax(mx[2], u.z);
         }
         __syncthreads();
-        // ---- phase B: lane l bins row l's landings of the staged realizations
-        if (kind_l == KIND_SAMPLE) {
-          const int64_t sc = s_l % Nc;
-          const int64_t li = sc % a.nx, lj = (sc / a.nx) % a.ny, lk = sc / nxy;
-          const uint32_t hb = smem_u32(hist) + (uint32_t)lane * 4u;
-          for (int w = warp; w < cn; w += nwarps) {
-            const U3<RT> u = ubuf[(size_t)w * a.spw + q_l];
-            int di, dj, dk;
-            if constexpr (sizeof(RT) == 4) {
-              di = land_offset(u.x, a.act.c[0][a_l], a.act.th[0][a_l]);
-              dj = land_offset(u.y, a.act.c[1][a_l], a.act.th[1][a_l]);
-              dk = land_offset(u.z, a.act.c[2][a_l], a.act.th[2][a_l]);
-            } else {
-              // x' = x + (v + a) dt from the cell centre, cell() = floor(x' / dx)
-              const double x = __dmul_rn((double)li + 0.5, a.dx), y = __dmul_rn((double)lj + 0.5, a.dx);
-              const double z = __dmul_rn((double)lk + 0.5, a.dx);
-              const double xp = __dadd_rn(x, __dmul_rn(__dadd_rn(u.x, a.act.d64[0][a_l]), a.dt));
-              const double yp = __dadd_rn(y, __dmul_rn(__dadd_rn(u.y, a.act.d64[1][a_l]), a.dt));
-              const double zp = __dadd_rn(z, __dmul_rn(__dadd_rn(u.z, a.act.d64[2][a_l]), a.dt));
-              const double fx = floor(__ddiv_rn(xp, a.dx)) - (double)li;
-              const double fy = floor(__ddiv_rn(yp, a.dx)) - (double)lj;
-              const double fz = floor(__ddiv_rn(zp, a.dx)) - (double)lk;
-              di = (fabs(fx) <= (double)h) ? (int)fx : h + 1;
-              dj = (fabs(fy) <= (double)h) ? (int)fy : h + 1;
-              dk = (fabs(fz) <= (double)h) ? (int)fz : h + 1;
-            }
-            if (di < -h || di > h || dj < -h || dj > h || dk < -h || dk > h) {
-              atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
-              continue;
-            }
-            const uint32_t b = (uint32_t)(((dk + h) * L + (dj + h)) * L + (di + h));
-            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + b * 128u), "r"(1u));
-          }
+        if (!try_rank) {
+          phase_b(cn);
+          __syncthreads();
         }
-        __syncthreads();
       }
       // the extreme u of each state: lanes of equal q_t are lane + multiples of spw
       for (int off = 16; off >= a.spw; off >>= 1) {
@@ -205,7 +279,101 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
         }
       }
       __syncthreads();
+      if (try_rank) {
+        // ---- rank counting (FP32): per state a fine table over the fine
+        // coordinates (floor(u) - n0) S + rho(frac u) of its extremes; the
+        // slice falls back to phase B when a table cannot be formed or the
+        // tables do not fit the window memory
+        if (tid < a.spw) {
+          const int q = tid;
+          Geo3 g{};
+          long long cells = 0;
+          if (kind(sl * a.spw + q) == KIND_SAMPLE) {
+            cells = 1;
+            for (int x = 0; x < 3 && cells > 0; ++x) {
+              float umn = INFINITY, umx = -INFINITY;
+              for (int w = 0; w < nwarps; ++w) {
+                umn = fminf(umn, (float)sbox[((size_t)w * a.spw + q) * 6 + x]);
+                umx = fmaxf(umx, (float)sbox[((size_t)w * a.spw + q) * 6 + 3 + x]);
+              }
+              if (!(umn > -1e6f) || !(umx < 1e6f) || umx - umn > 1024.f) {
+                cells = -1;   // non-finite, far or widely spread u (a sub-grid overflow): phase B
+                break;
+              }
+              const int S = a.act.D[x] + 1;
+              g.n0[x] = (int)floorf(umn);
+              g.fmin[x] = fine3(umn, g.n0[x], S, a.act.T[x], a.act.D[x]);
+              g.G[x] = fine3(umx, g.n0[x], S, a.act.T[x], a.act.D[x]) - g.fmin[x] + 1;
+              cells *= (long long)(g.G[x] + 1);
+            }
+          }
+          s_geo[q] = g;
+          s_cells[q] = cells;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          long long tot = 0;
+          bool fit = true;
+          for (int q = 0; q < a.spw; ++q) {
+            if (s_cells[q] < 0) fit = false;
+            s_geo[q].base = (int)min(tot, (long long)nb * 32);
+            tot += max(s_cells[q], 0LL);
+          }
+          fit = fit && tot <= (long long)nb * 32;
+          s_rank = fit ? 1 : 0;
+          s_total = fit ? (int)tot : 0;
+        }
+        __syncthreads();
+        if (s_rank) {
+          // one count per realization at its fine coordinate (the window
+          // memory is zero between slices)
+          if (kind_t == KIND_SAMPLE) {
+            const Geo3 g = s_geo[q_t];
+            const int Py = g.G[1] + 1, Pz = g.G[2] + 1;
+            const uint32_t hb = smem_u32(hist);
+            for (int w = w0; w < a.N; w += wstride) {
+              const U3<RT> u = ubuf[(size_t)w * a.spw + q_t];
+              int X = fine3((float)u.x, g.n0[0], a.act.D[0] + 1, a.act.T[0], a.act.D[0]) - g.fmin[0];
+              int Y = fine3((float)u.y, g.n0[1], a.act.D[1] + 1, a.act.T[1], a.act.D[1]) - g.fmin[1];
+              int Z = fine3((float)u.z, g.n0[2], a.act.D[2] + 1, a.act.T[2], a.act.D[2]) - g.fmin[2];
+              X = min(max(X, 0), g.G[0] - 1);
+              Y = min(max(Y, 0), g.G[1] - 1);
+              Z = min(max(Z, 0), g.G[2] - 1);
+              const uint32_t idx = (uint32_t)(g.base + ((X + 1) * Py + (Y + 1)) * Pz + (Z + 1));
+              asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + 4u * idx), "r"(1u));
+            }
+          }
+          __syncthreads();
+          // in-place inclusive prefix sums along z, y and x (the zero border
+          // planes stay zero): P[x][y][z] = sum of counts up to (x, y, z)
+          for (int q = 0; q < a.spw; ++q) {
+            if (s_cells[q] <= 0) continue;
+            const Geo3 g = s_geo[q];
+            const int Gx = g.G[0], Gy = g.G[1], Gz = g.G[2], Py = Gy + 1, Pz = Gz + 1;
+            uint32_t *P = hist + g.base;
+            for (int ln = tid; ln < Gx * Gy; ln += blockDim.x) {
+              uint32_t *r = P + ((ln / Gy + 1) * Py + (ln % Gy + 1)) * Pz;
+              for (int z = 1; z <= Gz; ++z) r[z] += r[z - 1];
+            }
+            __syncthreads();
+            for (int ln = tid; ln < Gx * Gz; ln += blockDim.x) {
+              uint32_t *r = P + (ln / Gz + 1) * Py * Pz + (ln % Gz + 1);
+              for (int y = 1; y <= Gy; ++y) r[y * Pz] += r[(y - 1) * Pz];
+            }
+            __syncthreads();
+            for (int ln = tid; ln < Gy * Gz; ln += blockDim.x) {
+              uint32_t *r = P + (ln / Gz + 1) * Pz + (ln % Gz + 1);
+              for (int x = 1; x <= Gx; ++x) r[x * Py * Pz] += r[(x - 1) * Py * Pz];
+            }
+            __syncthreads();
+          }
+        } else {
+          phase_b(a.N);   // every realization is staged
+          __syncthreads();
+        }
+      }
     }
+    const int rank_mode = s_rank, rank_total = s_total;
     // ---- emit (warp 0): ascending bins (dk, dj, di) of the row's box, sink
     // folded, R from counts
     if (warp == 0) {
@@ -216,6 +384,8 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
       int e = 0;
       uint32_t sink = 0;
       int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+      Geo3 gl{};
+      if (rank_mode && kind_l == KIND_SAMPLE) gl = s_geo[q_l];
       if (kind_l == KIND_SAMPLE) {
         RT umn[3] = {(RT)INFINITY, (RT)INFINITY, (RT)INFINITY}, umx[3] = {-(RT)INFINITY, -(RT)INFINITY, -(RT)INFINITY};
         for (int w = 0; w < nwarps; ++w) {
@@ -234,6 +404,9 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
             lo[x] = box_offset64(umn[x], a.act.d64[x][a_l], pos[x], a.dx, a.dt, h);
             hi[x] = box_offset64(umx[x], a.act.d64[x][a_l], pos[x], a.dx, a.dt, h);
           }
+          // (phase B counted the landings outside the window; rank counting
+          // counts the rows that have some)
+          if (rank_mode && (lo[x] < -h || hi[x] > h)) atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
           lo[x] = max(lo[x], -h);
           hi[x] = min(hi[x], h);
         }
@@ -241,7 +414,7 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
           for (int dj = lo[1]; dj <= hi[1]; ++dj)
             for (int di = lo[0]; di <= hi[0]; ++di) {
               const int b = ((dk + h) * L + (dj + h)) * L + (di + h);
-              const uint32_t n = hist[b * 32 + lane];
+              const uint32_t n = rank_mode ? rank_count(gl, di, dj, dk) : hist[b * 32 + lane];
               if (!n) continue;
               const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
               const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
@@ -273,10 +446,15 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
         for (int dk = lo[2]; dk <= hi[2]; ++dk)
           for (int dj = lo[1]; dj <= hi[1]; ++dj)
             for (int di = lo[0]; di <= hi[0]; ++di) {
-              uint32_t *hp = hist + (((dk + h) * L + (dj + h)) * L + (di + h)) * 32 + lane;
-              const uint32_t n = *hp;
+              uint32_t n;
+              if (rank_mode) {
+                n = rank_count(gl, di, dj, dk);
+              } else {
+                uint32_t *hp = hist + (((dk + h) * L + (dj + h)) * L + (di + h)) * 32 + lane;
+                n = *hp;
+                *hp = 0;
+              }
               if (!n) continue;
-              *hp = 0;
               const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
               const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
               const int64_t cp = (kp * a.ny + jp) * a.nx + ip;
@@ -332,6 +510,8 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
       loc_max = max(loc_max, (unsigned long long)W);
     }
     __syncthreads();
+    if (rank_mode)   // the window memory goes back to zero for the next slice
+      for (int i = tid; i < rank_total; i += blockDim.x) hist[i] = 0;
   }
   if (tid == 0) {
     atomicAdd(&a.cnt[CNT_NNZ], loc_tot);
@@ -369,6 +549,12 @@ static mdp_status arg3(const char *msg) {
 extern "C" mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_actions3d *actions,
                                   int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
                                   void *stream, mdp_model *out) {
+  return mdp_build3d_ex(env, grid, actions, N, subgrid_L, objs_h, n_obj, nullptr, stream, out);
+}
+
+extern "C" mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_actions3d *actions,
+                                     int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
+                                     const mdp_build3d_opts *opts, void *stream, mdp_model *out) {
   if (!out) return arg3("out is NULL");
   *out = nullptr;
   mdp_status s = check_device();
@@ -412,6 +598,26 @@ extern "C" mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, 
     ba.act.F[a] = (float)actions->table_h[4 * a + 3];
   }
   for (int x = 0; x < 3; ++x) axis_constants(ba.act.dl[x], A, ba.act.c[x], ba.act.th[x]);
+  // rank counting tables: the distinct step thresholds of each axis
+  bool rank_ok = prec == MDP_FP32 && !(opts && opts->per_action);
+  for (int x = 0; x < 3; ++x) {
+    std::vector<float> T;
+    for (int a = 0; a < A; ++a)
+      if (ba.act.th[x][a] < 2.0f) T.push_back(ba.act.th[x][a]);
+    std::sort(T.begin(), T.end());
+    T.erase(std::unique(T.begin(), T.end()), T.end());
+    if ((int)T.size() > kRank3) {
+      rank_ok = false;
+      T.resize(kRank3);
+    }
+    ba.act.D[x] = (int32_t)T.size();
+    for (int i = 0; i < kRank3; ++i) ba.act.T[x][i] = i < (int)T.size() ? T[i] : 2.0f;
+    for (int a = 0; a < A; ++a) {
+      int le = (int)T.size() + 1;   // an integer displacement never steps
+      if (ba.act.th[x][a] < 2.0f) le = (int)(std::upper_bound(T.begin(), T.end(), ba.act.th[x][a]) - T.begin());
+      ba.act.le[x][a] = (int8_t)le;
+    }
+  }
 
   mdp_model_t *m = new mdp_model_t();
   memset(m, 0, sizeof(*m));
@@ -498,6 +704,7 @@ extern "C" mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, 
 
   ba.nx = grid->nx; ba.ny = grid->ny; ba.nz = grid->nz; ba.nt = grid->nt; ba.K = env->K; ba.N = N; ba.A = A;
   ba.A_pad = A_pad; ba.spw = m->spw; ba.L = subgrid_L; ba.h = h; ba.row_cap = row_cap;
+  ba.rank_ok = (rank_ok && m->spw <= kRankSpw) ? 1 : 0;
   ba.Nc = m->Nc; ba.nS = m->nS; ba.n_slices = m->n_slices; ba.rows_pad = m->rows_pad;
   ba.lam = (float)lam; ba.dx = grid->dx; ba.dt = grid->dt;
   ba.vbar = env->vbar; ba.modes = env->modes; ba.Y = Y; ba.gbar = env->gbar;

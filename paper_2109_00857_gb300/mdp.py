@@ -114,6 +114,7 @@ SIGNATURES = {
     "mdp_solve_multi": (C.c_int, [P, C.c_int32, P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_solve_noalloc": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, P, P, P, P]),
     "mdp_build3d": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, P, P]),
+    "mdp_build3d_ex": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, P, P, P]),
     "mdp_rollout": (C.c_int, [P, P, P, C.c_int32, P, P, C.c_int32, P, C.c_int32, P, P, P, P, P]),
     "mdp_sample_coeffs": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_uint64, C.c_uint64,
                                     C.c_int32, P, P]),
@@ -300,16 +301,23 @@ def mdp_build(denv: DeviceEnv, N: Optional[int] = None, subgrid_L: Optional[int]
     return Model(h.value, denv.precision)
 
 
+class MdpBuild3DOpts(C.Structure):
+    _fields_ = [("per_action", C.c_int32)]
+
+
 def mdp_build3d(denv: DeviceEnv3D, objs: Sequence[int] = (MDP_OBJ_TIME,), N: Optional[int] = None,
-                subgrid_L: Optional[int] = None, stream=None) -> Model:
-    """The build on a 3-D grid; the model works with mdp_solve / mdp_export_csr."""
+                subgrid_L: Optional[int] = None, stream=None, per_action: bool = False) -> Model:
+    """The build on a 3-D grid; the model works with mdp_solve / mdp_export_csr.
+    per_action=True counts one increment per (realization, action) on every
+    slice (mdp_build3d_opts.per_action; the same model)."""
     e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
     ob = np.ascontiguousarray(objs, dtype=np.int32)
     h = P()
     N = denv.env.N if N is None else N
     L = denv.env.L if subgrid_L is None else subgrid_L
-    _check(load().mdp_build3d(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
-                              _stream(stream), C.byref(h)), "mdp_build3d")
+    o = MdpBuild3DOpts(1 if per_action else 0)
+    _check(load().mdp_build3d_ex(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
+                                 C.byref(o), _stream(stream), C.byref(h)), "mdp_build3d")
     return Model(h.value, denv.precision)
 
 

@@ -102,3 +102,31 @@ def test_3d_argument_errors(mdp):
     with pytest.raises(mdp.MdpError) as ei:   # 16-bit successor offsets
         mdp.mdp_build3d(mdp.DeviceEnv3D(big, mdp.MDP_FP32), subgrid_L=3)
     assert ei.value.code == -1
+
+
+RANK_CASES = {
+    # one state per slice (24 actions), two (10 actions) and four (6 actions)
+    "cube_spw1": lambda: inputs.cube(nx=12, ny=11, nz=5, nt=4, N=300, with_gbar=True, objectives=(0, 1, 2)),
+    "spw2": lambda: inputs.make_env3d(nx=9, ny=8, nz=6, nt=4, K=2, N=200, L=9, sigma=(0.3, 0.2), seed=5,
+                                      amplitude=0.6, n_headings=5, elevations=(0.0, 0.7), speeds=(0.9,)),
+    "spw4": lambda: inputs.make_env3d(nx=10, ny=7, nz=4, nt=3, K=3, N=150, L=7, sigma=(0.3, 0.2, 0.1), seed=6,
+                                      amplitude=0.7, n_headings=3, elevations=(-0.5, 0.5), speeds=(1.0,)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RANK_CASES))
+def test_rank_counting_equals_per_action_counting(mdp, case):
+    """FP32: counting each realization once at its fine coordinates (box sums
+    of the prefix table) gives the same model as one increment per
+    (realization, action) -- counts, successors and R bit for bit."""
+    env = RANK_CASES[case]()
+    objs = env.objectives if env.gbar is not None else (0,)
+    d = mdp.DeviceEnv3D(env, mdp.MDP_FP32)
+    fast = mdp.mdp_build3d(d, objs=objs)
+    ref = mdp.mdp_build3d(d, objs=objs, per_action=True)
+    assert fast.info().nnz == ref.info().nnz
+    for o in range(len(objs)):
+        a = export_np(mdp, fast, o)
+        b = export_np(mdp, ref, o)
+        assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])), (case, o)
+        assert np.array_equal(a[3].view(np.uint32), b[3].view(np.uint32)), (case, o)
