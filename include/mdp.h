@@ -176,7 +176,13 @@ typedef enum {
                                 * other state has V_{k+1}(s) = V_k(s) exactly, so iterates, policy,
                                 * residuals and sweep count equal MDP_SOLVE_JACOBI_FULL bit for bit */
   MDP_SOLVE_LAYERED = 1,      /* one backward pass over time layers t = nt-1..0 (same fixed point) */
-  MDP_SOLVE_JACOBI_FULL = 2   /* Jacobi sweeps over every state in every sweep */
+  MDP_SOLVE_JACOBI_FULL = 2,  /* Jacobi sweeps over every state in every sweep */
+  MDP_SOLVE_WARM = 16         /* flag, OR-ed into MDP_SOLVE_JACOBI or _JACOBI_FULL of mdp_solve
+                                * (one objective): V on entry is V_0 (e.g. the previous plan's
+                                * values when replanning, Sec. V) instead of 0; V[|S|] is reset to 0.
+                                * This MDP reaches its exact fixed point from any V_0 within nt + 1
+                                * sweeps, so with tol = 0 the result equals the cold start's bit for
+                                * bit; a V_0 near the fixed point needs fewer sweeps */
 } mdp_solve_method;
 
 typedef struct {
@@ -190,8 +196,9 @@ typedef struct {
 /* Value iteration on the model's P and the R of objective slot obj.
  * V: device [|S|+1] float (FP32) or double (FP64_CHECK), V[|S|] = 0 (sink);
  * policy: device int16 [|S|], argmax_a with the lowest index winning ties,
- * -1 for terminal and obstacle start states.  Jacobi starts from V = 0 and
- * stops when max|V_{k+1} - V_k| <= tol or after max_sweeps sweeps
+ * -1 for terminal and obstacle start states.  Jacobi starts from V = 0 (or,
+ * with MDP_SOLVE_WARM, from V as given) and stops when max|V_{k+1} - V_k| <= tol
+ * or after max_sweeps sweeps
  * (0 = nt + 1, which reaches the exact fixed point of this time-layered MDP).
  * Synchronises `stream` once to read the sweep count and residual. */
 mdp_status mdp_solve(mdp_model m, int32_t obj, int32_t method, double tol, int32_t max_sweeps,

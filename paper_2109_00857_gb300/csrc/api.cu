@@ -595,8 +595,12 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
     if (!V[o] || !policy[o]) return arg_fail("NULL V or policy");
     if (objs[o] < 0 || objs[o] >= m->n_obj) return arg_fail("objective slot out of range");
   }
+  const bool warm = (method & MDP_SOLVE_WARM) != 0;
+  method &= ~MDP_SOLVE_WARM;
   if (method != MDP_SOLVE_JACOBI && method != MDP_SOLVE_LAYERED && method != MDP_SOLVE_JACOBI_FULL)
     return arg_fail("method");
+  if (warm && (n != 1 || method == MDP_SOLVE_LAYERED))
+    return arg_fail("MDP_SOLVE_WARM applies to single-objective Jacobi solves");
   if (!(tol >= 0) && !(tol < 0)) return arg_fail("tol is NaN");
   if (max_sweeps < 0) return arg_fail("max_sweeps must be >= 0");
   if (max_sweeps == 0) max_sweeps = m->nt + 1;
@@ -639,7 +643,12 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   io.Vtmp[0] = (n == 1 && jac) ? m->Vtmp : nullptr;
   for (int t = 0; t < n_tables; ++t) io.table[t] = static_cast<char *>(tables) + tbytes * t;
   for (int o = 0; o < n && ce == cudaSuccess; ++o) ce = cudaMemsetAsync(sd + o * blk, 0, sizeof(double) * 4, st);
-  if (ce == cudaSuccess && n == 1) ce = cudaMemsetAsync(V[0], 0, vbytes, st);
+  if (ce == cudaSuccess && n == 1) {
+    if (warm)   // V_0 as given; the sink stays 0
+      ce = cudaMemsetAsync(static_cast<char *>(V[0]) + fsz * (size_t)m->nS, 0, fsz, st);
+    else
+      ce = cudaMemsetAsync(V[0], 0, vbytes, st);
+  }
   if (ce == cudaSuccess && io.Vtmp[0]) ce = cudaMemsetAsync(io.Vtmp[0], 0, vbytes, st);
   if (ce == cudaSuccess && tables) ce = cudaMemsetAsync(tables, 0, tbytes * n_tables, st);
   SolveArgs a;

@@ -24,6 +24,7 @@ STATUS = {0: "MDP_OK", -1: "MDP_ERR_ARG", -2: "MDP_ERR_OOM", -3: "MDP_ERR_SUBGRI
 MDP_OBJ_TIME, MDP_OBJ_ENERGY, MDP_OBJ_NET_ENERGY = 0, 1, 2
 MDP_FP32, MDP_FP64_CHECK = 0, 1
 MDP_SOLVE_JACOBI, MDP_SOLVE_LAYERED, MDP_SOLVE_JACOBI_FULL = 0, 1, 2
+MDP_SOLVE_WARM = 16   # flag: Jacobi starts from the given V
 
 P = C.c_void_p
 
@@ -342,8 +343,13 @@ def mdp_export_csr(model: Model, obj: int = 0, stream=None):
 
 
 def mdp_solve(model: Model, obj: int = 0, method: int = MDP_SOLVE_JACOBI, tol: float = 0.0,
-              max_sweeps: int = 0, V=None, policy=None, stream=None):
-    """Returns (V, policy, MdpSolveStats); V / policy are torch device tensors."""
+              max_sweeps: int = 0, V=None, policy=None, stream=None, warm: bool = False):
+    """Returns (V, policy, MdpSolveStats); V / policy are torch device tensors.
+    warm=True (MDP_SOLVE_WARM): Jacobi starts from the given V instead of 0."""
+    if warm:
+        if V is None:
+            raise ValueError("a warm start needs V")
+        method |= MDP_SOLVE_WARM
     import torch
     info = mdp_model_info(model)
     if V is None:
