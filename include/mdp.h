@@ -390,6 +390,11 @@ typedef struct {
                                     fields with freshly drawn coefficients (on-board
                                     re-planning, Sec. V); its V / policy cover those
                                     nt - start_t layers (index (t - start_t)*nx*ny + c) */
+  const float *V0_h;             /* host [|S|+1] or NULL: starting values of a Jacobi request
+                                    (tol > 0; MDP_SOLVE_WARM), e.g. the V polled from an
+                                    earlier request on the same env and start_t; NULL: start
+                                    from 0; exact requests ignore it.  Must stay valid until
+                                    the request completes */
 } mdp_request;
 
 typedef struct {

@@ -146,8 +146,22 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   }
   mdp_solve_stats ss{};
   // the exact fixed point is reached by one backward pass over the layers
-  // (the same values as Jacobi to tol = 0) with far fewer Bellman backups
-  const int32_t method = r.tol == 0.0 ? MDP_SOLVE_LAYERED : MDP_SOLVE_JACOBI;
+  // (the same values as Jacobi to tol = 0) with far fewer Bellman backups;
+  // a Jacobi request may start from the caller's values (replanning warm)
+  int32_t method = r.tol == 0.0 ? MDP_SOLVE_LAYERED : MDP_SOLVE_JACOBI;
+  if (method == MDP_SOLVE_JACOBI && r.V0_h) {
+    ce = cudaMemcpyAsync(V, r.V0_h, sizeof(float) * (size_t)(nS + 1), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+      job.status = cuda_fail(ce, "serve warm start");
+      job.error = mdp_last_error();
+      dev_free(V, st);
+      dev_free(pi, st);
+      free_model_on_stream(m, st);
+      cudaStreamSynchronize(st);
+      return;
+    }
+    method |= MDP_SOLVE_WARM;
+  }
   s = mdp_solve(m, 0, method, r.tol, 0, V, pi, st, &ss);
   if (s == MDP_OK) {
     job.V.resize((size_t)nS + 1);

@@ -96,7 +96,7 @@ class MdpRequest(C.Structure):
                 ("target_i", C.c_int32), ("target_j", C.c_int32), ("target_w", C.c_int32),
                 ("target_h", C.c_int32), ("sigma_scale", C.c_double), ("seed", C.c_uint64),
                 ("N", C.c_int32), ("objective", C.c_int32), ("tol", C.c_double),
-                ("start_t", C.c_int32)]
+                ("start_t", C.c_int32), ("V0_h", P)]
 
 
 class MdpResult(C.Structure):
@@ -455,6 +455,7 @@ class Server:
         self.handle = h.value
         self._envs = []
         self._start_t = {}
+        self._keep = {}   # ticket -> host starting values the server reads
 
     def register(self, denv: DeviceEnv, subgrid_L: Optional[int] = None) -> int:
         e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
@@ -467,7 +468,9 @@ class Server:
         return eid.value
 
     def submit(self, env_id, start, target, target_size=(2, 2), sigma_scale=1.0, seed=0, N=1000,
-               objective=MDP_OBJ_TIME, tol=0.0, start_t=0) -> int:
+               objective=MDP_OBJ_TIME, tol=0.0, start_t=0, V0=None) -> int:
+        """V0: host float32 array [|S|+1] starting a Jacobi request (tol > 0), e.g.
+        the V polled from an earlier request; kept alive until the poll."""
         r = MdpRequest()
         r.env_id = env_id
         r.start_i, r.start_j = start
@@ -475,9 +478,18 @@ class Server:
         r.target_w, r.target_h = target_size
         r.sigma_scale, r.seed, r.N, r.objective, r.tol = sigma_scale, seed, N, objective, tol
         r.start_t = start_t
+        v0 = None
+        if V0 is not None:
+            v0 = np.ascontiguousarray(V0, dtype=np.float32)
+            env = self._envs[env_id]
+            if v0.size != (env.nt - start_t) * env.Nc + 1:
+                raise ValueError("V0 must hold |S| + 1 values of the request's horizon")
+            r.V0_h = v0.ctypes.data_as(P)
         t = C.c_uint64()
         _check(load().mdp_serve_submit(self.handle, C.byref(r), C.byref(t)), "mdp_serve_submit")
         self._start_t[t.value] = start_t
+        if v0 is not None:
+            self._keep[t.value] = v0
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 0, env_id: Optional[int] = None, want_V=False):
@@ -495,6 +507,7 @@ class Server:
                                      pi.ctypes.data_as(P) if pi is not None else None)
         if code == -10:
             return None
+        self._keep.pop(int(ticket), None)
         _check(code, "mdp_serve_poll")
         return res, V, pi
 

@@ -152,3 +152,28 @@ def test_replanning_from_a_later_time_step(mdp):
     assert np.array_equal(V, Vd) and np.array_equal(pi, pid)
     s0 = probe["start"][1] * env.nx + probe["start"][0]
     assert res.V_start == V[s0] and res.pi_start == pi[s0]
+
+
+def test_jacobi_request_warm_started_from_an_earlier_result(mdp):
+    """Replanning warm (Sec. V): a Jacobi request started from the exact
+    values of an earlier request with the same parameters stops after one
+    sweep with those values bit for bit; started cold it needs more sweeps."""
+    env = inputs.energy(nx=24, ny=20, nt=8, N=300, L=15)
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    srv = mdp.Server(8 << 30, 2)
+    eid = srv.register(d)
+    kw = dict(start=(3, 3), target=(15, 14), sigma_scale=0.9, seed=77, N=300)
+    t0 = srv.submit(eid, **kw)                     # exact: the layered pass
+    r0, V0, pi0 = srv.poll(t0, timeout_ms=120000, env_id=eid, want_V=True)
+    assert r0.status == 0
+    tw = srv.submit(eid, tol=1e-3, V0=V0, **kw)    # Jacobi from the exact values
+    rw, Vw, piw = srv.poll(tw, timeout_ms=120000, env_id=eid, want_V=True)
+    tc = srv.submit(eid, tol=1e-3, **kw)           # Jacobi from 0
+    rc, Vc, pic = srv.poll(tc, timeout_ms=120000, env_id=eid, want_V=True)
+    assert rw.status == 0 and rc.status == 0
+    assert rw.sweeps == 1 and rc.sweeps > 1
+    assert np.array_equal(Vw.view(np.uint32), V0.view(np.uint32))
+    assert np.array_equal(piw, pi0)
+    with pytest.raises(ValueError):
+        srv.submit(eid, tol=1e-3, V0=V0[:-1], **kw)
+    srv.close()
