@@ -136,3 +136,37 @@ def test_overflow_is_counted():
     e = env3(nx, ny, nz, nt, N=5, L=3, vbar=vb, actions=np.array([[0.0, 0.0, 0.0, 0.0]]))
     m = oracle.build3d(e)
     assert m.overflow > 0
+
+
+def test_vertical_mode_gives_gaussian_layer_offsets():
+    """One unit mode along z with coefficient variance sigma^2 and mean vertical
+    velocity mu, an action with no displacement: the layer offset
+    floor(1/2 + mu + Y) of a landing is n with probability
+    Phi((n + 1/2 - mu) / sigma) - Phi((n - 1/2 - mu) / sigma).  Counts of every
+    start state are checked against it within 5 standard errors (+1)."""
+    from math import erf, sqrt
+    nx, ny, nz, nt, N = 3, 3, 15, 2, 4000
+    mu, sig = 0.3, 1.1
+    vb = np.zeros((nt, nz, ny, nx, 3))
+    vb[..., 2] = mu
+    e = env3(nx, ny, nz, nt, N=N, L=11, vbar=vb, actions=np.array([[0.0, 0.0, 0.0, 0.0]]))
+    e.modes = np.zeros((nt, 1, nz, ny, nx, 3))
+    e.modes[..., 2] = 1.0
+    e.sigma = np.array([sig])
+    m = oracle.build3d(e)
+    assert m.overflow == 0
+
+    def Phi(x):
+        return 0.5 * (1.0 + erf(x / sqrt(2.0)))
+
+    checked = 0
+    for k in range(5, 10):   # interior layers: every offset within +-5 stays inside
+        s = (k * ny + 1) * nx + 1           # t = 0, centre column
+        lo, hi = m.rowptr[s], m.rowptr[s + 1]
+        got = dict(zip(m.col[lo:hi].tolist(), m.cnt[lo:hi].tolist()))
+        for n in range(-5, 6):
+            p = Phi((n + 0.5 - mu) / sig) - Phi((n - 0.5 - mu) / sig)
+            c = got.get(e.Nc + s + n * nx * ny, 0)
+            assert abs(c - N * p) <= 5 * sqrt(N * p * (1 - p)) + 1, (k, n, c, N * p)
+            checked += 1
+    assert checked == 55
