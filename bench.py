@@ -54,18 +54,29 @@ def workload(name, rank=0, nt=None):
     return env
 
 
+def source_digest(paths):
+    """sha256 of the code of C/CUDA sources with comments and whitespace
+    removed (a comment edit keeps the digest; any code edit changes it)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for src in paths:
+        with open(os.path.join(ROOT, src)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def kernel_counters(kernel, workload_name):
     """ncu per-unit counters of a kernel (profiles/counters.json), or None when
-    the kernel's sources changed since the capture or the workload differs."""
-    import hashlib
+    the kernel's code changed since the capture or the workload differs."""
     try:
         with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
             c = json.load(f)[kernel]
-        h = hashlib.sha256()
-        for src in c["sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != c["sha256"] or not workload_name.startswith(c.get("workload", "large")):
+        if source_digest(c["sources"]) != c["code_sha256"] or \
+                not workload_name.startswith(c.get("workload", "large")):
             return None
         return c
     except Exception:

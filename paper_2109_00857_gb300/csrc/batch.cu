@@ -9,14 +9,16 @@
 // sizes the Bellman stages for the widest slice.  Then each item is set up
 // through the same path as mdp_build (allocations, coefficient table, cell
 // classes) without launching its build.
-// Run: one persistent warp-per-slice launch per states-per-warp class
-// builds its items' slices from one work queue; one CTA launch finishes the
-// slices any item deferred;
-// each Jacobi sweep is a one-block plan launch that cuts every item's
-// recomputed layers (those whose inputs changed in the previous sweep) into
-// chunks of equal size, and one launch whose CTAs take one chunk each (an
-// item stops on its own residual); one launch
-// finalizes all.  The whole sequence (with the per-item coefficient draws,
+// Run: one persistent warp-per-slice launch per (states per warp, mode
+// count) group builds its items' slices from one work queue; one CTA launch
+// finishes the slices any item deferred;
+// the solve runs batched steps -- with tol = 0 the layered pass (step k
+// updates layer nt - k of every item that has it, in place: the exact fixed
+// point), with tol > 0 Jacobi sweeps (the layers whose inputs changed in the
+// previous sweep; an item stops on its own residual) -- each step, per solve
+// class (grouped sweep or warp per slice), a one-block plan launch that cuts
+// the items' slices into chunks of equal size and one launch whose CTAs take
+// one chunk each; one launch finalizes all.  The whole sequence (with the per-item coefficient draws,
 // cell classes, clears and the status copies) is captured once into a CUDA
 // graph and replayed on every run.
 #include <algorithm>

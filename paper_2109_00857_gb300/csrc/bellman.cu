@@ -4,12 +4,15 @@
 //
 // Bellman backup (Sec. II-B): Q(s,a) = R(s,a) + sum_j P_j V(s'_j),
 // V_{k+1}(s) = max_a Q(s,a), pi(s) = argmax_a Q(s,a) (lowest index wins ties).
-// One warp per slice: lane l streams its row's (bin, count) words from the
-// slice's columns (128 B per k, coalesced), gathers V(s') from the next time
-// layer (L2 resident), and a segmented butterfly over the A_pad lanes of a
-// state gives the max and argmax.  Residual max|V_{k+1} - V_k| is reduced on
-// the device; a sweep whose predecessor met the tolerance exits at once, so a
-// fixed launch sequence needs no host round trip between sweeps.
+// The slices' entry columns are copied into shared-memory stages by TMA bulk
+// copies and the successors' values V(s') gathered from the next time layer.
+// Two kernels with the same results bit for bit: warp per slice (lane l sums
+// row l; a redux.sync key or a segmented butterfly over the A_pad lanes of a
+// state gives the max and argmax), and for one state per slice the grouped
+// sweep (four states per warp step, each lane summing four rows and keeping a
+// running max, a 3-step shuffle per state).  Residual max|V_{k+1} - V_k| is
+// reduced on the device; a sweep whose predecessor met the tolerance exits at
+// once, so a fixed launch sequence needs no host round trip between sweeps.
 #include <cfloat>
 
 #include "build_common.cuh"
