@@ -1,6 +1,6 @@
 // build_warp.cuh -- the warp-per-slice FP32 build (steps a2-a6 fused) as a
 // device function, shared by the single-model kernel (build_warp.cu) and the
-// batched kernel (batch.cu).
+// batched kernel (build_warp_batch.cu).
 //
 // A warp works alone on one slice (spw states x A_pad actions, 32 rows) with
 // private shared memory and no block-level barrier.  The landing offset of

@@ -7,9 +7,12 @@
 // a tolerance.  Requests wait in a FIFO queue; max_slots worker threads, each
 // with its own CUDA stream, take the head of the queue as soon as a slot is
 // free and the request's device-memory estimate fits the HBM budget, then build
-// and solve it (mdp_build + Jacobi mdp_solve).  Requests admitted while others
-// run overlap with them on the GPU (continuous batching); each retires on its
-// own, copies V and the policy to host memory and releases its device memory.
+// and solve it: mdp_build over the remaining horizon t = start_t..nt-1, then
+// mdp_solve -- the layered pass for an exact request (tol = 0), Jacobi sweeps
+// to tol otherwise (from the request's starting values V0_h when given).
+// Requests admitted while others run overlap with them on the GPU (continuous
+// batching); each retires on its own, copies V and the policy to host memory
+// and releases its device memory.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
