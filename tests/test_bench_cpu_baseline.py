@@ -29,3 +29,14 @@ def test_all_cores_baseline_runs_on_two_processes():
     env = inputs.tiny(nx=12, ny=10, nt=4, N=40)
     out = bench.cpu_baseline_all_cores(env, seconds=0.2, workers=2)
     assert out["cores"] == 2 and out["value"] > 0 and out["kind"] == "oracle"
+
+
+def test_counter_digest_ignores_comments_but_not_code(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// header\n__global__ void k(int *x) {\n  x[0] = 1;  /* one */\n}\n")
+    b.write_text("/* another\n   header */\n__global__ void k(int *x) {   // a kernel\n      x[0] = 1;\n}\n")
+    c.write_text("// header\n__global__ void k(int *x) {\n  x[0] = 2;  /* one */\n}\n")
+    assert bench.source_digest([str(a)]) == bench.source_digest([str(b)])
+    assert bench.source_digest([str(a)]) != bench.source_digest([str(c)])
