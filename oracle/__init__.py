@@ -85,7 +85,7 @@ def lib():
             l.orc_build.argtypes = [C.POINTER(Problem), C.c_int64, C.c_int64, C.c_int32, P,
                                     C.c_int32, P, P, P, P, P, P]
             l.orc_build.restype = C.c_int
-            l.orc_vi_jacobi.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P, C.c_double,
+            l.orc_vi_jacobi.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P, P, C.c_double,
                                         C.c_int32, P, P, P, P]
             l.orc_vi_jacobi.restype = C.c_int
             l.orc_vi_backward.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int64, P, P, P, P,
@@ -249,7 +249,10 @@ def fixed_mask(env) -> np.ndarray:
     return ((env.obstacle != 0) | (tgt != 0)).astype(np.uint8).reshape(-1)
 
 
-def vi_jacobi(m, R, fixed, tol=0.0, max_sweeps=None, nt=None):
+def vi_jacobi(m, R, fixed, tol=0.0, max_sweeps=None, nt=None, V0=None):
+    """Jacobi value iteration (Sec. II-B) from v_0 = V0 (length nS or nS + 1;
+    the sink entry is 0 regardless) or from 0.  Pinned by backward induction,
+    dense brute force, and a dense one-sweep Bellman operator from random V0."""
     nS, A = m.nS, m.A
     if max_sweeps is None:
         max_sweeps = (nt + 1) if nt is not None else 10 ** 6
@@ -258,7 +261,11 @@ def vi_jacobi(m, R, fixed, tol=0.0, max_sweeps=None, nt=None):
     sw, res = C.c_int32(0), C.c_double(0.0)
     Rc = np.ascontiguousarray(R, dtype=np.float64)
     fx = np.ascontiguousarray(fixed, dtype=np.uint8)
-    lib().orc_vi_jacobi(nS, A, _p(m.rowptr), _p(m.col), _p(m.prob), _p(Rc), _p(fx), tol,
+    v0 = None
+    if V0 is not None:
+        v0 = np.ascontiguousarray(np.asarray(V0, dtype=np.float64)[:nS])
+        assert v0.shape == (nS,)
+    lib().orc_vi_jacobi(nS, A, _p(m.rowptr), _p(m.col), _p(m.prob), _p(Rc), _p(fx), _p(v0), tol,
                         max_sweeps, _p(V), _p(pi), C.byref(sw), C.byref(res))
     return V, pi, sw.value, res.value
 

@@ -298,11 +298,17 @@ void orc_q_values(int64_t nS, int32_t A, const int64_t *rowptr, const int64_t *c
 }
 
 int orc_vi_jacobi(int64_t nS, int32_t A, const int64_t *rowptr, const int64_t *col,
-                  const double *prob, const double *R, const uint8_t *fixed, double tol,
-                  int32_t max_sweeps, double *V, int32_t *pi, int32_t *sweeps, double *residual) {
+                  const double *prob, const double *R, const uint8_t *fixed, const double *V0,
+                  double tol, int32_t max_sweeps, double *V, int32_t *pi, int32_t *sweeps,
+                  double *residual) {
   double *Vold = (double *)malloc(sizeof(double) * (size_t)(nS + 1));
   if (!Vold) return -2;
-  for (int64_t s = 0; s <= nS; ++s) { V[s] = 0.0; Vold[s] = 0.0; } /* v_0 = 0, V(sink) = 0 */
+  /* v_0: the caller's values (V0 != NULL) or 0 everywhere; V(sink) = 0 always */
+  for (int64_t s = 0; s <= nS; ++s) {
+    const double v0 = (V0 && s < nS) ? V0[s] : 0.0;
+    V[s] = v0;
+    Vold[s] = v0;
+  }
   int32_t k = 0;
   double res = 0.0;
   while (k < max_sweeps) {

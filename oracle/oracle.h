@@ -81,10 +81,13 @@ int orc_build(const orc_problem *p, int64_t u_begin, int64_t u_end, int32_t max_
 /* Gauss-Jacobi value iteration on the paper-layout CSR model (Sec. II-B).
  * rows = A*nS, row r = a*nS + s; col < nS or col == nS (sink, V = 0).
  * fixed[s] != 0 marks terminal/obstacle start states: pi[s] = -1 there.
- * Stops when max|V_{k+1}-V_k| <= tol or after max_sweeps sweeps. */
+ * v_0 = V0[0..nS) when V0 is non-NULL (e.g. a previous plan's values when
+ * replanning), else 0.  Stops when max|V_{k+1}-V_k| <= tol or after
+ * max_sweeps sweeps. */
 int orc_vi_jacobi(int64_t nS, int32_t A, const int64_t *rowptr, const int64_t *col,
-                  const double *prob, const double *R, const uint8_t *fixed, double tol,
-                  int32_t max_sweeps, double *V, int32_t *pi, int32_t *sweeps, double *residual);
+                  const double *prob, const double *R, const uint8_t *fixed, const double *V0,
+                  double tol, int32_t max_sweeps, double *V, int32_t *pi, int32_t *sweeps,
+                  double *residual);
 
 /* Backward induction over time layers t = nt-1 .. 0 with the same per-(s,a)
  * operation order (transitions go from layer t to t+1 or the sink only). */

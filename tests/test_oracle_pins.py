@@ -399,3 +399,62 @@ def test_dense_brute_force_value_iteration_5x5():
                 assert pio[s] == -1
                 continue
             assert Q[pio[s], s] >= Q[:, s].max() - 1e-12
+
+
+def _dense_P(m, nS, A, N):
+    """Dense P[a][s][s'] (s' = nS is the sink) from the oracle's CSR counts."""
+    P = np.zeros((A, nS, nS + 1))
+    for r in range(A * nS):
+        a, s = divmod(r, nS)
+        lo, hi = m.rowptr[r], m.rowptr[r + 1]
+        P[a, s, m.col[lo:hi]] += m.cnt[lo:hi] / N
+    return P
+
+
+def test_vi_from_given_values_one_sweep_is_the_bellman_operator():
+    """One Jacobi sweep from an arbitrary v_0 (Sec. II-B update
+    v_1(s) = max_a [R(s,a) + sum_s' P(s'|s,a) v_0(s')], V(sink) = 0), written
+    out with a dense numpy matrix product, against the oracle started from
+    the same v_0; also k sweeps = the dense operator applied k times."""
+    e = inputs.energy(nx=6, ny=5, nt=4, N=90, L=11, objectives=(0, 1, 2))
+    m = oracle.build(e, objs=(0, 1, 2))
+    nS, A = e.nS, e.A
+    P = _dense_P(m, nS, A, e.N)
+    fx = oracle.fixed_mask(e)
+    rng = np.random.default_rng(17)
+    for o in range(3):
+        V0 = rng.normal(0.0, 30.0, nS)
+        V = np.concatenate([V0, [0.0]])
+        for k in (1, 2, 3):
+            Q = m.R[o].reshape(A, nS) + P @ V
+            V = np.concatenate([Q.max(axis=0), [0.0]])
+            Vo, pio, sw, res = oracle.vi_jacobi(m, m.R[o], fx, tol=-1.0, max_sweeps=k, V0=V0)
+            assert sw == k and Vo[nS] == 0.0
+            np.testing.assert_allclose(Vo, V, rtol=1e-12, atol=1e-9)
+            best = Q.max(axis=0)
+            for s in range(nS):
+                if fx[s]:
+                    assert pio[s] == -1
+                else:
+                    assert Q[pio[s], s] >= best[s] - 1e-9 * max(1.0, abs(best[s]))
+
+
+def test_vi_from_any_values_reaches_the_cold_fixed_point_in_nt_plus_1_sweeps():
+    """Transitions go from layer t to t+1 or the sink (Sec. II-A, t' = t + dt),
+    so after k sweeps layers t >= nt - k no longer depend on v_0: from any v_0
+    the iteration is at the cold start's fixed point after nt sweeps (bit for
+    bit: the same operations on the same operands) and sweep nt + 1 changes
+    nothing."""
+    e = inputs.tiny(nx=9, ny=8, nt=6, N=70, r_term=3.0)
+    m = oracle.build(e)
+    fx = oracle.fixed_mask(e)
+    Vc, pic, swc, resc = oracle.vi_jacobi(m, m.R[0], fx, tol=0.0, nt=e.nt)
+    rng = np.random.default_rng(5)
+    for scale in (1.0, 1e3):
+        V0 = rng.normal(0.0, scale, e.nS)
+        Vw, piw, sww, resw = oracle.vi_jacobi(m, m.R[0], fx, tol=0.0, nt=e.nt, V0=V0)
+        assert sww <= e.nt + 1 and resw == 0.0
+        assert np.array_equal(Vw, Vc) and np.array_equal(piw, pic)
+    # V0 = 0 given explicitly is the cold start
+    Vz, piz, swz, resz = oracle.vi_jacobi(m, m.R[0], fx, tol=0.0, nt=e.nt, V0=np.zeros(e.nS))
+    assert np.array_equal(Vz, Vc) and swz == swc
