@@ -700,8 +700,8 @@ def main():
                   "counters": cb["summary"] if cb else "stale or absent: kernel changed since the capture",
                   "ms_per_launch": kmean,
                   "peak_basis": f"{sms} SMs x 4 issue slots x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
-    # the grouped sweep serves one-state slices (A_pad = 32) up to 13 columns
-    bell_name = "bellman_kernel_g" if env.A > 16 and info.max_row_nnz <= 13 else "bellman_kernel"
+    # the ring sweep serves one-state slices (A_pad = 32)
+    bell_name = "bellman_kernel_r" if env.A > 16 else "bellman_kernel"
     roof_bell = {"kernel": bell_name, "objectives_per_sweep": n_fused, "bound": "hbm",
                  "achieved": bell_achieved, "peak": hbm, "unit": "GB/s", "frac": bell_achieved / hbm,
                  "traffic": cs["dram_bytes_per_unit"] * n_slices if cs else None,

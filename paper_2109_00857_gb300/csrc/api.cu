@@ -525,13 +525,16 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   m->nnz_domain = (int64_t)c[CNT_DOMAIN];
   m->max_row_nnz = (int32_t)c[CNT_MAXROW];
   m->samples = (int64_t)c[CNT_SAMPLES];
-  // -- compaction: the bump-allocated columns are contiguous, so shrink the pool
-  if (!(opts && opts->no_compact) && m->pool_cols < cap_cols) {
+  // -- compaction: the columns in use move into a pool of exactly that size,
+  // in slice order (a run of consecutive slices is then one contiguous copy
+  // for the solver)
+  if (!(opts && opts->no_compact)) {
     uint32_t *np = nullptr;
     TRY(dev_alloc((void **)&np, (size_t)std::max<uint64_t>(m->pool_cols, 1) * 128, st));
-    if (m->pool_cols) TRY(cudaMemcpyAsync(np, m->pool, (size_t)m->pool_cols * 128, cudaMemcpyDeviceToDevice, st));
+    TRY(launch_pool_reorder(m->pool, np, m->slice_off, m->slice_w, m->n_slices, st));
     dev_free(m->pool, st);
     m->pool = np;
+    m->pool_ordered = 1;
     cap_cols = std::max<uint64_t>(m->pool_cols, 1);
   }
   m->device_bytes = (int64_t)cap_cols * 128 + 5 * m->n_slices + 3 * m->rows_pad + (int64_t)fsz * m->rows_pad * n_obj +
@@ -660,6 +663,7 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
   a.err = reinterpret_cast<int *>(sd + 2);
   a.nt = m->nt;
+  a.pool_ordered = m->pool_ordered;
   if (active) {
     a.work = reinterpret_cast<unsigned long long *>(sd + blk * n);
     a.lflags = reinterpret_cast<uint8_t *>(sd + blk * n + max_sweeps);

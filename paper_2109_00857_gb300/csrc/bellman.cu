@@ -13,6 +13,7 @@
 // running max, a 3-step shuffle per state).  Residual max|V_{k+1} - V_k| is
 // reduced on the device; a sweep whose predecessor met the tolerance exits at
 // once, so a fixed launch sequence needs no host round trip between sweeps.
+#include <algorithm>
 #include <cfloat>
 
 #include "build_common.cuh"
@@ -123,6 +124,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
   return true;
 }
+// The same bounded wait, but each test may suspend the warp (up to ~20 us,
+// resumed as soon as the phase completes) instead of spinning, so waiting
+// warps leave the issue slots to the others.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_suspend(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+  return true;
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
@@ -153,7 +174,8 @@ struct PipeRange {
   int64_t s_lo, s_hi;     // states whose V this launch writes
   int stage_bytes;        // bytes per stage
   int dtab_smem;          // 1: delta table staged in shared memory
-  int grouped;            // 1: bellman_kernel_g (kGS states per warp step)
+  int grouped;            // 1: bellman_kernel_g (kGS states per warp step); 2: bellman_kernel_ws
+                          // (stage_bytes = entry bytes per slot)
 };
 
 // one stage holds a slice's entry columns (at most wcap of them)
@@ -706,6 +728,338 @@ __global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_kernel_g(SolveArgs a,
   bellman_body_g<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
 }
 
+// ---- warp-specialized sweep: a producer warp stages rounds of slices ----
+// Models with one state per slice (A_pad = 32).  Each CTA has kWsCons
+// consumer warps and one producer warp, and walks its block of consecutive
+// slices in rounds: a round holds up to kWsCons consecutive slices (as many as
+// fit a slot's entry capacity) and consumer warp w takes slice w of every
+// round, so the CTA's warps gather V(s') from one small window of layer t+1
+// that L1 keeps.  The producer copies a round into one of kWsSlots
+// shared-memory slots with TMA bulk copies -- the slices' entry columns (one
+// copy when the pool is in slice order, else one per slice), then for every
+// objective the round's R values in one copy (consecutive slices have
+// consecutive R rows) -- completing on the slot's full barrier, and writes
+// each slice's columns, cell class and current values (loaded one round
+// ahead) into the slot's table; the consumers arrive on the slot's empty
+// barrier once they have read it, and the producer refills it.  Slots are
+// sized by the bytes the slices really have, not by the widest slice.  Lane l
+// of a consumer sums row l (action l) in ascending column order, so every Q is
+// the same float as in the other kernels, and the max over the 32 actions is
+// one redux.sync on an order-preserving key with the lowest winning action by
+// ballot (FP64: a butterfly): values and policy equal theirs bit for bit.
+constexpr int kWsCons = 31;     // consumer warps per CTA (+ 1 producer = 1024 threads)
+constexpr int kWsSlots = 3;     // round slots
+
+struct WsHdr {
+  uint64_t full[kWsSlots];      // producer arrival + the round's copied bytes
+  uint64_t empty[kWsSlots];     // one arrival per consumer warp
+  int2 round[kWsSlots];         // (first slice, slices in the round); 0 slices ends the block
+  int2 slice[kWsSlots][32];     // (entry byte offset in the slot, W | cell class << 8) per slice
+};
+__host__ __device__ constexpr size_t ws_hdr_bytes() { return (sizeof(WsHdr) + 127) & ~(size_t)127; }
+// the slices' current values, [kWsSlots][32]
+template <typename RT, int NO>
+__host__ __device__ constexpr size_t ws_old_bytes() { return (kWsSlots * 32 * sizeof(VPack<RT, NO>) + 127) & ~(size_t)127; }
+template <typename RT>
+__host__ __device__ constexpr int ws_r_bytes(int n_obj) { return n_obj * 32 * 32 * (int)sizeof(RT); }
+
+template <typename RT, int NO>
+__device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
+                                                int64_t b_hi, const PipeRange &pr, unsigned char *sm,
+                                                double *wmax, int *s_flag) {
+  using Pk = VPack<RT, NO>;
+  unsigned live = (1u << NO) - 1u;
+  if (k > 1) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (v.res[o] && __longlong_as_double((long long)v.res[o][k - 2]) <= a.tol) live &= ~(1u << o);
+  }
+  if (!live) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // one read of the error word for the whole CTA (an earlier launch timed out)
+  if (tid == 0) *s_flag = *(volatile int *)a.err;
+  __syncthreads();
+  if (*s_flag) return;
+  if (a.work && k >= 1 && blockIdx.x == 0 && tid == 0) a.work[k - 1] = (unsigned long long)(pr.sl_hi - pr.sl_lo);
+  if (b_hi <= b_lo) return;
+
+  WsHdr *hdr = reinterpret_cast<WsHdr *>(sm);
+  Pk *olds = reinterpret_cast<Pk *>(sm + ws_hdr_bytes());   // [kWsSlots][32]
+  constexpr int kRB = 32 * (int)sizeof(RT);                // one objective's R values of a slice
+  constexpr int kRBytes = ws_r_bytes<RT>(NO);
+  const int ecap = pr.stage_bytes;                         // entry bytes per slot
+  const int slot_bytes = kRBytes + ecap;
+  unsigned char *slots = sm + ws_hdr_bytes() + ws_old_bytes<RT, NO>();
+  if (tid < kWsSlots) {
+    mbar_init(smem_u32(&hdr->full[tid]), 1);
+    mbar_init(smem_u32(&hdr->empty[tid]), kWsCons);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t full0 = smem_u32(&hdr->full[0]), empty0 = smem_u32(&hdr->empty[0]);
+  const uint32_t slots0 = smem_u32(slots);
+
+  if (warp == kWsCons) {
+    // ---------------------------------------------------------- producer
+    const uint64_t stream_policy = l2_evict_first();
+    const RT *myR = nullptr;   // lane o copies objective o's R rows
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (lane == o) myR = v.R[o];
+    int64_t sl = b_lo;
+    bool failed = false;
+    // lane l: slice sl + l of the next round -- pool column, columns, cell
+    // class and current values -- loaded before the wait for its slot
+    uint32_t off = 0;
+    int W = 0, cls = 0;
+    Pk old{};
+    auto fetch = [&]() {
+      off = 0;
+      W = 0;
+      cls = 0;
+      if (lane < kWsCons && sl + lane < b_hi) {
+        const int64_t x = sl + lane;
+        off = __ldg(a.slice_off + x);
+        W = __ldg(a.slice_w + x);
+        cls = __ldg(a.cls + x);   // spw = 1: state = slice
+        old = v.in[x];
+      }
+    };
+    fetch();
+    int slot = 0;
+    uint32_t ph = 0;   // phase parity of the slot's current round
+    for (int r = 0;; ++r) {
+      if (r >= kWsSlots && !mbar_wait_suspend(empty0 + 8u * (uint32_t)slot, ph ^ 1u)) {
+        if (lane == 0) atomicOr(a.err, 1);
+        failed = true;
+        break;
+      }
+      int n = 0, tot = 0, e = 0;
+      const uint32_t off0 = __shfl_sync(0xffffffffu, off, 0);
+      if (sl < b_hi) {
+        int cum = W * 128;   // inclusive scan of the entry bytes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int x = __shfl_up_sync(0xffffffffu, cum, d);
+          if (lane >= d) cum += x;
+        }
+        const bool valid = lane < kWsCons && sl + lane < b_hi;
+        n = __popc(__ballot_sync(0xffffffffu, valid && cum <= ecap));   // a prefix of the lanes
+        tot = __shfl_sync(0xffffffffu, cum, (n > 0 ? n : 1) - 1);
+        e = cum - W * 128;
+        if (lane < n) {
+          hdr->slice[slot][lane] = make_int2(e, W | (cls << 8));
+          olds[slot * 32 + lane] = old;
+        }
+      }
+      __syncwarp();   // the slot's table is written before lane 0 arrives (release)
+      const uint32_t fb = full0 + 8u * (uint32_t)slot;
+      if (lane == 0) {
+        hdr->round[slot] = make_int2((int)sl, n);
+        if (n > 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the slot's earlier reads
+          mbar_expect_tx(fb, (uint32_t)(tot + NO * n * kRB));
+        } else {
+          mbar_arrive(fb);   // no more rounds: the consumers stop here
+        }
+      }
+      __syncwarp();
+      if (n == 0) break;
+      const uint32_t sbase = slots0 + (uint32_t)(slot * slot_bytes);
+      if (a.pool_ordered) {
+        // the round's slices are back to back in the pool: one copy
+        if (lane == 0 && tot > 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bulk_g2s_stream(sbase + (uint32_t)kRBytes, a.pool + (size_t)off0 * 32, (uint32_t)tot, fb, stream_policy);
+        }
+      } else if (lane < n && W > 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_g2s_stream(sbase + (uint32_t)(kRBytes + e), a.pool + (size_t)off * 32, (uint32_t)W * 128u,
+                        fb, stream_policy);
+      }
+      if (lane < NO) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_g2s_stream(sbase + (uint32_t)(lane * 32 * kRB), myR + (size_t)sl * 32, (uint32_t)(n * kRB), fb,
+                        stream_policy);
+      }
+      __syncwarp();
+      sl += n;
+      fetch();   // the next round's slices
+      if (++slot == kWsSlots) {
+        slot = 0;
+        ph ^= 1u;
+      }
+    }
+    // After a timeout the consumers may have stopped reading: wait (bounded)
+    // for the copies of the last rounds issued, whose slots were not reused,
+    // so that none is still in flight when the CTA exits.  (Normally every
+    // round was waited for by the consumers, and the end-of-block round has
+    // reused one of these slots, so this must not run then.)
+    if (failed) {
+      for (int i = 0; i < kWsSlots; ++i) {
+        slot = (slot + kWsSlots - 1) % kWsSlots;   // the last rounds, newest first
+        if (slot == kWsSlots - 1) ph ^= 1u;
+        mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- consumers
+    const int nS = (int)a.nS, Nc = (int)a.Nc;
+    const int s_lo = (int)pr.s_lo, s_hi = (int)pr.s_hi;
+    const RT invN = (RT)1 / (RT)a.N;
+    const bool act_ok = lane < a.A;
+    int16_t *mypol = v.pol[0];   // lane o < NO writes objective o's policy
+#pragma unroll
+    for (int o = 1; o < NO; ++o)
+      if (lane == o) mypol = v.pol[o];
+    const bool mylive = lane < NO && ((live >> lane) & 1u);
+    float rf[NO];
+    double rd[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      rf[o] = 0.f;
+      rd[o] = 0.0;
+    }
+    uint8_t *chg_out = a.lflags ? a.lflags + (size_t)(k % 3) * (a.nt + 1) : nullptr;
+    int t_cur = -1, t_end = 0;
+    bool chg = false;
+    int slot = 0;
+    uint32_t ph = 0;
+    for (;;) {
+      if (!mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph)) {
+        if (lane == 0) atomicOr(a.err, 1);
+        break;
+      }
+      const int2 rdesc = hdr->round[slot];
+      if (rdesc.y == 0) break;
+      const bool mine = warp < rdesc.y;
+      const int s = rdesc.x + warp;   // spw = 1: state = slice
+      Acc<RT> acc[NO];
+      RT Rv[NO];
+      Pk old{};
+      int wc = 0;
+      if (mine) {
+        const int2 sd = hdr->slice[slot][warp];
+        wc = sd.y;
+        const int W = wc & 0xFF;
+        const unsigned char *sb = slots + (size_t)slot * slot_bytes;
+        const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb + kRBytes + sd.x) + lane;
+        const int sn = (s + Nc <= nS) ? s + Nc : nS;
+        const Pk *Vn = v.in + sn;
+#pragma unroll 4
+        for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
+          const uint32_t w = ent[kk * 32];
+          const Pk g = Vn[(int)(int16_t)(w & 0xFFFFu)];
+#pragma unroll
+          for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, g.v[o], a.N);
+        }
+        const RT *Rs = reinterpret_cast<const RT *>(sb) + warp * 32 + lane;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) Rv[o] = Rs[o * 32 * 32];
+        old = olds[slot * 32 + warp];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8u * (uint32_t)slot);   // the slot is read
+      if (++slot == kWsSlots) {
+        slot = 0;
+        ph ^= 1u;
+      }
+      if (!mine) continue;
+      RT qv[NO];
+      int qa[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        RT q = act_ok ? acc[o].q(Rv[o], invN) : -(RT)INFINITY;
+        int ia = lane;
+        if constexpr (sizeof(RT) == 4) {
+          // order-preserving key (-0 keys like +0): the max in one redux,
+          // the lowest lane (= lowest action) among the maxima by ballot
+          const uint32_t bits = __float_as_uint((float)q + 0.0f);
+          const uint32_t key = bits ^ ((uint32_t)((int32_t)bits >> 31) | 0x80000000u);
+          const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+          ia = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
+          q = __shfl_sync(0xffffffffu, q, ia);
+        } else {
+#pragma unroll
+          for (int m = 1; m < 32; m <<= 1) {
+            const RT oq = __shfl_xor_sync(0xffffffffu, q, m);
+            const int oa = __shfl_xor_sync(0xffffffffu, ia, m);
+            if (oq > q || (oq == q && oa < ia)) {
+              q = oq;
+              ia = oa;
+            }
+          }
+        }
+        qv[o] = q;
+        qa[o] = ia;
+      }
+      if (s < s_lo || s >= s_hi) continue;
+      const bool term = (wc >> 8) != CLS_FREE;
+      Pk nv;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const bool upd = (live >> o) & 1u;
+        nv.v[o] = upd ? qv[o] : old.v[o];
+        if (upd) {
+          if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv[o] - old.v[o]));
+          else rd[o] = fmax(rd[o], fabs(qv[o] - old.v[o]));
+        }
+      }
+#pragma unroll
+      for (int o = NO; o < Pk::W; ++o) nv.v[o] = (RT)0;
+      int myqa = qa[0];
+#pragma unroll
+      for (int o = 1; o < NO; ++o)
+        if (lane == o) myqa = qa[o];
+      if (mylive) mypol[s] = term ? (int16_t)-1 : (int16_t)myqa;
+      if (lane == 0) v.out[s] = nv;
+      if (chg_out) {
+        if (s >= t_end) {   // entered a later layer: publish the finished one
+          if (chg && lane == 0) chg_out[t_cur] = 1;
+          chg = false;
+          t_cur = s / Nc;
+          t_end = (t_cur + 1) * Nc;
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {   // bitwise: -0 vs +0 counts as a change
+          if constexpr (sizeof(RT) == 4) chg |= __float_as_uint(nv.v[o]) != __float_as_uint(old.v[o]);
+          else chg |= __double_as_longlong(nv.v[o]) != __double_as_longlong(old.v[o]);
+        }
+      }
+    }
+    if (chg_out && chg && lane == 0) chg_out[t_cur] = 1;
+    if (v.res[0] && lane == 0) {
+#pragma unroll
+      for (int o = 0; o < NO; ++o) wmax[warp * NO + o] = (sizeof(RT) == 4) ? (double)rf[o] : rd[o];
+    }
+  }
+  if (v.res[0]) {
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {   // thread o publishes objective o
+      if (tid == o) {
+        double m = 0.0;
+        for (int i = 0; i < kWsCons; ++i) m = fmax(m, wmax[i * NO + o]);
+        if (m > 0.0) atomicMax(&v.res[o][k - 1], (unsigned long long)__double_as_longlong(m));
+      }
+    }
+  }
+}
+
+template <typename RT, int NO>
+__global__ void __launch_bounds__(32 * (kWsCons + 1), 1) bellman_kernel_ws(SolveArgs a, VSet<RT, NO> v, int k,
+                                                                         PipeRange pr) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double wmax[kWsCons * NO];
+  __shared__ int s_flag;
+  if (a.lflags && k >= 1 && !active_range(a, k, pr, blockIdx.x == 0)) return;
+  const int64_t total = pr.sl_hi - pr.sl_lo;
+  const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
+  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
+  bellman_body_ws<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, &s_flag);
+}
+
 // Plan of batched Jacobi sweep k (one block): per model, the slices of the
 // layers whose inputs changed in sweep k-1 (nothing once the model met the
 // tolerance or ran max_sweeps), with the model's flags for sweep k+1
@@ -927,9 +1281,39 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
     Va[i] = Vb[i];
 }
 
+// Warp-specialized sweep: per slot the R rows of up to 32 slices and the
+// entry bytes of a round; three slots of ~44 KB (FP32, three objectives) keep
+// about two rounds of copies in flight while one is read and leave the rest of
+// the SM's 256 KB to L1.  A slot always holds the widest slice.
+constexpr size_t kWsSmem = 132 * 1024;
+
+template <typename RT, int NO>
+static int ws_entry_bytes(int wcap) {
+  const long per_slot = (long)((kWsSmem - ws_hdr_bytes() - ws_old_bytes<RT, NO>()) / kWsSlots) - ws_r_bytes<RT>(NO);
+  long e = std::max<long>(per_slot, (long)wcap * 128);
+  return (int)(e & ~127L);
+}
+
 template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
   pr->dtab_smem = 0;
+  if (a.spw == 1) {   // one state per slice: the warp-specialized sweep, any width
+    pr->grouped = 2;
+    pr->stage_bytes = ws_entry_bytes<RT, NO>(a.wcap);
+    *smem = ws_hdr_bytes() + ws_old_bytes<RT, NO>() + (size_t)kWsSlots * (ws_r_bytes<RT>(NO) + pr->stage_bytes);
+    cudaError_t e = allow_max_smem((const void *)bellman_kernel_ws<RT, NO>);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel_ws<RT, NO>, 32 * (kWsCons + 1), *smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t b = (int64_t)num_sms() * per_sm;
+    const int64_t want = (slices + 2 * kWsCons - 1) / (2 * kWsCons);   // >= 2 rounds per CTA
+    if (b > want) b = want;
+    if (b < 1) b = 1;
+    *blocks = (int)b;
+    return cudaSuccess;
+  }
   // grouped sweep for one state per slice while kWarpsG warps x kDepth
   // stages of kGS slots fit one CTA's shared memory (slices up to 13
   // columns); wider models take the warp-per-slice kernel
@@ -1010,7 +1394,9 @@ __global__ void finalize_multi_kernel(const double *stats_base, size_t blk, int 
 template <typename RT, int NO>
 static void launch_sweep(const SolveArgs &a, const VSet<RT, NO> &v, int k, const PipeRange &pr, int blocks,
                          size_t smem, cudaStream_t st) {
-  if (pr.grouped)
+  if (pr.grouped == 2)
+    bellman_kernel_ws<RT, NO><<<blocks, 32 * (kWsCons + 1), smem, st>>>(a, v, k, pr);
+  else if (pr.grouped)
     bellman_kernel_g<RT, NO><<<blocks, 32 * kWarpsG, smem, st>>>(a, v, k, pr);
   else
     bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, k, pr);
@@ -1210,6 +1596,54 @@ static cudaError_t exclusive_scan(int64_t *x, int64_t n, int64_t *scratch, cudaS
   if (blocks > 65535) blocks = 65535;
   scan_add_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, scratch);
   return cudaGetLastError();
+}
+
+// One warp per slice: the slice's W columns are W*128 contiguous bytes in
+// both pools, copied as 16-byte vectors; then the new offset is recorded.
+__global__ void pool_reorder_kernel(const uint32_t *__restrict__ pool, uint32_t *__restrict__ out,
+                                    uint32_t *slice_off, const uint8_t *__restrict__ slice_w,
+                                    const int64_t *__restrict__ new_off, int64_t n_slices) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = wid; sl < n_slices; sl += nwarps) {
+    const int W = slice_w[sl];
+    const int64_t no = new_off[sl];
+    if (W) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(pool + (size_t)slice_off[sl] * 32);
+      uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)no * 32);
+      for (int i = lane; i < W * 8; i += 32) dst[i] = src[i];
+    }
+    __syncwarp();
+    if (lane == 0) slice_off[sl] = (uint32_t)no;
+  }
+}
+
+__global__ void slice_width_kernel(const uint8_t *__restrict__ slice_w, int64_t *x, int64_t n_slices) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n_slices; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = i < n_slices ? (int64_t)slice_w[i] : 0;
+}
+
+cudaError_t launch_pool_reorder(const uint32_t *pool, uint32_t *out, uint32_t *slice_off, const uint8_t *slice_w,
+                                int64_t n_slices, cudaStream_t st) {
+  const int64_t n = n_slices + 1;
+  int64_t need = n, nn = n;   // offsets, then the scan's tile sums
+  while (nn > 1) { nn = (nn + 1023) / 1024; need += nn; }
+  int64_t *x = nullptr;
+  cudaError_t e = dev_alloc((void **)&x, sizeof(int64_t) * (size_t)(need + 1), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = std::min<int64_t>(8192, (n + 255) / 256);
+  slice_width_kernel<<<(unsigned)blocks, 256, 0, st>>>(slice_w, x, n_slices);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = exclusive_scan(x, n, x + n, st);
+  if (e == cudaSuccess) {
+    blocks = std::min<int64_t>(num_sms() * 16, (n_slices + 7) / 8);
+    if (blocks < 1) blocks = 1;
+    pool_reorder_kernel<<<(unsigned)blocks, 256, 0, st>>>(pool, out, slice_off, slice_w, x, n_slices);
+    e = cudaGetLastError();
+  }
+  dev_free(x, st);
+  return e;
 }
 
 template <typename RT>

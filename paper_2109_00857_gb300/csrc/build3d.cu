@@ -773,10 +773,11 @@ extern "C" mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *gri
   m->nnz_domain = (int64_t)c[CNT_DOMAIN];
   m->max_row_nnz = (int32_t)c[CNT_MAXROW];
   m->samples = (int64_t)c[CNT_SAMPLES];
-  if (m->pool_cols < cap_cols) {   // compaction: the bump-allocated columns are contiguous
+  {   // compaction into a pool of exactly the columns in use, in slice order
     uint32_t *np = nullptr;
     TRY3(dev_alloc((void **)&np, (size_t)std::max<uint64_t>(m->pool_cols, 1) * 128, st));
-    if (m->pool_cols) TRY3(cudaMemcpyAsync(np, m->pool, (size_t)m->pool_cols * 128, cudaMemcpyDeviceToDevice, st));
+    TRY3(launch_pool_reorder(m->pool, np, m->slice_off, m->slice_w, m->n_slices, st));
+    m->pool_ordered = 1;
     dev_free(m->pool, st);
     m->pool = np;
     cap_cols = std::max<uint64_t>(m->pool_cols, 1);

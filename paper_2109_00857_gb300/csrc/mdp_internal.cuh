@@ -12,6 +12,9 @@
 //   sink           sinkc[ir] realizations end in the sink s' = |S| (V = 0)
 //   R              R[o * rows_pad + ir]        (float or double), rows_pad = n_slices * 32
 // Warps read a slice column (32 lanes x 4 B = 128 B) per k: fully coalesced.
+// A slice's columns are contiguous; the build allocates them in completion
+// order and its compaction moves them into slice order (pool_ordered), so
+// that the columns of consecutive slices are one contiguous range.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -138,6 +141,8 @@ struct mdp_model_t {
   int32_t launches;
   int64_t deferred;           // slices the full-window kernel built
   int device;
+  int32_t pool_ordered;       // 1: the pool holds the slices in slice order, back to back
+                              // (slice_off[sl + 1] = slice_off[sl] + slice_w[sl])
 };
 
 namespace mdpgb {
@@ -201,6 +206,7 @@ struct SolveArgs {
   uint8_t *lflags = nullptr;
   unsigned long long *work = nullptr;   // [max_sweeps] slices computed per sweep (or nullptr)
   int32_t nt = 0;
+  int32_t pool_ordered = 0;   // the model's pool_ordered: a run of slices is one contiguous copy
 };
 // batched solve (FP32): one Jacobi sweep over many models per launch
 struct BatchSolveItem {
@@ -255,6 +261,12 @@ cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, cons
                                  double *stats_d, cudaStream_t st);
 cudaError_t launch_jacobi(const SolveArgs &a, int precision, int max_sweeps, void *Va, void *Vb,
                           int16_t *policy, double *stats_d, cudaStream_t st);
+// Copies the slices' entry columns from `pool` (any order) into `out` in
+// slice order, back to back, and rewrites slice_off accordingly (a slice
+// without columns gets the offset where the next one starts).  `out` holds
+// the sum of slice_w columns.
+cudaError_t launch_pool_reorder(const uint32_t *pool, uint32_t *out, uint32_t *slice_off, const uint8_t *slice_w,
+                                int64_t n_slices, cudaStream_t st);
 // export
 cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_t *col,
                           int32_t *count, void *R, cudaStream_t st);

@@ -119,6 +119,7 @@ extern "C" mdp_status mdp_solve_noalloc(mdp_model m, int32_t obj, double tol, in
   a.A = m->A; a.A_pad = m->A_pad; a.spw = m->spw; a.N = m->N; a.nbins = m->nbins; a.tol = tol;
   a.err = reinterpret_cast<int *>(sd + 2);
   a.nt = m->nt;
+  a.pool_ordered = m->pool_ordered;
   if ((size_t)m->nt + 1 <= kNoAllocLayers) {
     a.work = reinterpret_cast<unsigned long long *>(scratch + kNoAllocVBytes + kNoAllocStatus);
     a.lflags = scratch + kNoAllocVBytes + kNoAllocStatus + kNoAllocWork;

@@ -328,17 +328,22 @@ def mdp_model_info(model: Model) -> MdpModelInfo:
     return info
 
 
-def mdp_export_csr(model: Model, obj: int = 0, stream=None):
-    """Paper-layout CSR (row = a*|S| + s) as torch device tensors (rowptr, col, count, R)."""
+def mdp_export_csr(model: Model, obj: int = 0, stream=None, with_entries: bool = True):
+    """Paper-layout CSR (row = a*|S| + s) as torch device tensors (rowptr, col, count, R);
+    with_entries=False skips col and count (returned as None)."""
     import torch
     info = mdp_model_info(model)
     rows = info.rows
     rowptr = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
-    col = torch.empty(max(info.nnz, 1), dtype=torch.int64, device="cuda")
-    cnt = torch.empty(max(info.nnz, 1), dtype=torch.int32, device="cuda")
+    col = cnt = None
+    if with_entries:
+        col = torch.empty(max(info.nnz, 1), dtype=torch.int64, device="cuda")
+        cnt = torch.empty(max(info.nnz, 1), dtype=torch.int32, device="cuda")
     R = torch.empty(rows, dtype=torch.float64 if model.precision else torch.float32, device="cuda")
     _check(load().mdp_export_csr(model.handle, obj, _ptr(rowptr), _ptr(col), _ptr(cnt), _ptr(R),
                                  _stream(stream)), "mdp_export_csr")
+    if not with_entries:
+        return rowptr, None, None, R
     return rowptr, col[:info.nnz], cnt[:info.nnz], R
 
 

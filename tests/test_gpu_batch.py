@@ -4,6 +4,7 @@ the model and values of building and solving it alone."""
 import numpy as np
 import pytest
 
+from conftest import oracle_end_to_end
 from paper_2109_00857_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -74,3 +75,18 @@ def test_batch_rejects_fp64_items(mdp):
     e = inputs.tiny()
     with pytest.raises(mdp.MdpError):
         mdp.Batch([mdp.DeviceEnv(e, mdp.MDP_FP64_CHECK)])
+
+
+def test_batch_members_match_the_oracle(mdp):
+    """Members of a batch (16 and 32 actions, different mode counts, grids and
+    horizons) against the oracle's build and value iteration of each member,
+    end to end: |dV| <= 1e-5 max(1, |V|) plus the exact effect of the FP32
+    build's count differences, policy equal up to ties within the same bound."""
+    envs = [inputs.batch_member(i, nx=12 + 3 * i, ny=11 + 2 * i, nt=4 + i, N=50 + 10 * i)
+            for i in range(3)]
+    assert len({e.A for e in envs}) > 1
+    b = mdp.Batch([mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs], tol=0.0)
+    b.run()
+    for i, e in enumerate(envs):
+        oracle_end_to_end(mdp, e, e.objectives[0], b.V[i].cpu().numpy(), b.policy[i].cpu().numpy())
+    b.close()

@@ -6,6 +6,7 @@ import time
 import numpy as np
 import pytest
 
+from conftest import oracle_end_to_end
 from paper_2109_00857_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -177,3 +178,37 @@ def test_jacobi_request_warm_started_from_an_earlier_result(mdp):
     with pytest.raises(ValueError):
         srv.submit(eid, tol=1e-3, V0=V0[:-1], **kw)
     srv.close()
+
+
+def _cut_request_env(env, t0, target, sigma_scale, seed, N):
+    """The environment a request describes: layers t0..nt-1 of the resident
+    fields, a 2x2 target block, sigma scaled, its own seed and N (mdp_id 0)."""
+    e = inputs.Environment(**{**env.__dict__})
+    e.nt = env.nt - t0
+    e.vbar, e.modes, e.obstacle = env.vbar[t0:], env.modes[t0:], env.obstacle[t0:]
+    e.gbar = env.gbar[t0:] if env.gbar is not None else None
+    e.target = inputs.target_block(env.nx, env.ny, target[0], target[1])
+    e.sigma = env.sigma * sigma_scale
+    e.seed, e.N, e.mdp_id, e.Y = seed, N, 0, None
+    return e
+
+
+@pytest.mark.parametrize("t0,objective", [(0, 0), (2, 2)])
+def test_served_request_matches_the_oracle(mdp, t0, objective):
+    """A served request (t0 = 0) and a replanning request from a later step
+    (t0 = 2: the remaining horizon on the resident fields with a fresh draw,
+    Sec. V) against the oracle's build and value iteration of the horizon the
+    request describes, end to end: |dV| <= 1e-5 max(1, |V|) plus the exact
+    effect of the FP32 build's count differences, policy equal up to ties
+    within the same bound."""
+    env = inputs.energy(nx=16, ny=14, nt=7, N=60, L=15, seed=23)
+    srv = mdp.Server(8 << 30, 2)
+    eid = srv.register(mdp.DeviceEnv(env, mdp.MDP_FP32))
+    probe = dict(start=(8, 3), target=(8, 10), sigma_scale=1.2, seed=41, N=60, objective=objective)
+    t = srv.submit(eid, start_t=t0, **probe)
+    res, V, pi = srv.poll(t, timeout_ms=60000, env_id=eid, want_V=True)
+    assert res.status == 0, mdp.load().mdp_last_error().decode()
+    srv.close()
+    e = _cut_request_env(env, t0, probe["target"], probe["sigma_scale"], probe["seed"], probe["N"])
+    assert V.shape == (e.nS + 1,)
+    oracle_end_to_end(mdp, e, objective, V, pi)

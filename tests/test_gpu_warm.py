@@ -7,6 +7,8 @@ stops it in fewer sweeps than the cold start."""
 import numpy as np
 import pytest
 
+import oracle
+from conftest import policy_tie_check
 from paper_2109_00857_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -72,3 +74,46 @@ def test_warm_start_argument_errors(mdp):
     with pytest.raises(mdp.MdpError) as ei:   # fused solves start cold
         mdp.mdp_solve_multi(model, (0, 0), method=mdp.MDP_SOLVE_JACOBI | mdp.MDP_SOLVE_WARM)
     assert ei.value.code == -1
+
+
+def test_warm_start_iterates_equal_the_oracle_from_the_same_values(mdp):
+    """Sweeps from a given v_0 (Sec. II-B update; replanning from a previous
+    plan, Sec. V) against the oracle's value iteration from the same v_0.
+    Check mode: after k = 1, 2, 3 sweeps and with a tolerance stop, V, policy,
+    sweep count and residual equal the oracle's (V to 1e-12) on the oracle's
+    own build.  FP32: on the GPU's exported P/R, |dV| <= 1e-5 max(1, |V|) and
+    the policy equals the oracle's up to ties."""
+    import torch
+    env = inputs.energy(nx=14, ny=12, nt=6, N=60, L=15, objectives=(0, 1, 2))
+    ref = oracle.build(env, objs=(0, 1, 2))
+    fx = oracle.fixed_mask(env)
+    m64 = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP64_CHECK), objs=(0, 1, 2))
+    m32 = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), objs=(0, 1, 2))
+    rng = np.random.default_rng(31)
+    for o in range(3):
+        V0 = rng.normal(0.0, 40.0, env.nS)
+        for k, tol in ((1, 0.0), (2, 0.0), (3, 0.0), (0, 5.0)):
+            V = torch.tensor(np.concatenate([V0, [99.0]]), dtype=torch.float64, device="cuda")
+            V, pi, st = mdp.mdp_solve(m64, o, tol=tol, max_sweeps=k, V=V, warm=True)
+            Vo, pio, sw, res = oracle.vi_jacobi(ref, ref.R[o], fx, tol=tol, max_sweeps=k or env.nt + 1,
+                                                V0=V0)
+            assert st.sweeps == sw and st.residual == pytest.approx(res, rel=1e-12, abs=1e-300)
+            np.testing.assert_allclose(V.cpu().numpy(), Vo, rtol=1e-12, atol=1e-12)
+            assert np.array_equal(pi.cpu().numpy(), pio)
+        rp, col, cnt, R = (x.cpu().numpy() for x in mdp.mdp_export_csr(m32, o))
+        om = oracle.model_from_csr(env.nS, env.A, env.N, rp, col, cnt)
+        R64 = R.astype(np.float64)
+        V0f = V0.astype(np.float32)
+        for k in (1, 3):
+            V = torch.tensor(np.concatenate([V0f, [0.0]]), dtype=torch.float32, device="cuda")
+            V, pi, st = mdp.mdp_solve(m32, o, tol=0.0, max_sweeps=k, V=V, warm=True)
+            Vo, pio, sw, res = oracle.vi_jacobi(om, R64, fx, tol=0.0, max_sweeps=k,
+                                                V0=V0f.astype(np.float64))
+            assert st.sweeps == sw
+            Vg = V.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(Vg - Vo) <= 1e-5 * np.maximum(1.0, np.abs(Vo)))
+            # the policy of sweep k is the argmax of the Q of the values before it
+            Vprev, _, _, _ = oracle.vi_jacobi(om, R64, fx, tol=0.0, max_sweeps=k - 1,
+                                              V0=V0f.astype(np.float64)) if k > 1 else \
+                (np.concatenate([V0f.astype(np.float64), [0.0]]), None, 0, 0)
+            policy_tie_check(pi.cpu().numpy(), pio, oracle.q_values(om, R64, Vprev))

@@ -69,3 +69,74 @@ def test_noalloc_solve_rejects_sizes_beyond_its_scratch(mdp):
     with pytest.raises(mdp.MdpError) as ei:
         mdp.mdp_solve_noalloc(m2, 0)
     assert ei.value.code == -1 and "states" in str(ei.value)
+
+
+def _pool_and_free():
+    """(used-memory high-water mark of the device's default memory pool after
+    resetting it, a function reading (pool high-water mark, free device
+    bytes)) through the CUDA driver API, which sees every stream-ordered
+    allocation on the device whichever runtime made it."""
+    import ctypes as C
+    cu = C.CDLL("libcuda.so.1")
+    dev = C.c_int()
+    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    USED_HIGH = 8   # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def reset():
+        zero = C.c_uint64(0)   # resets the high-water mark to the current use
+        assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, C.byref(zero)) == 0
+
+    def read():
+        hi = C.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, USED_HIGH, C.byref(hi)) == 0
+        free, total = C.c_size_t(), C.c_size_t()
+        assert cu.cuMemGetInfo_v2(C.byref(free), C.byref(total)) == 0
+        return hi.value, free.value
+    return reset, read
+
+
+def test_noalloc_solve_allocates_no_device_memory(mdp):
+    """The promise itself: on a warmed model, a call leaves the device
+    memory pool's used-memory high-water mark and the free device memory
+    exactly where they were (mdp_solve on the same model, for contrast,
+    allocates its scratch from that pool)."""
+    import torch
+    env = inputs.energy(nx=30, ny=26, nt=6, N=300)
+    model = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), objs=env.objectives)
+    V = torch.zeros(env.nS + 1, dtype=torch.float32, device="cuda")
+    pi = torch.zeros(env.nS, dtype=torch.int16, device="cuda")
+    mdp.mdp_solve_noalloc(model, 0, V=V, policy=pi)     # warm: module loaded, scratch address known
+    torch.cuda.synchronize()
+    reset, read = _pool_and_free()
+    reset()
+    before = read()
+    for _ in range(2):
+        mdp.mdp_solve_noalloc(model, 0, V=V, policy=pi)
+    torch.cuda.synchronize()
+    assert read() == before
+    reset()
+    hi0, _ = read()
+    mdp.mdp_solve(model, 0, tol=0.0, V=torch.zeros_like(V), policy=torch.zeros_like(pi))
+    torch.cuda.synchronize()
+    assert read()[0] > hi0   # the allocating solve does show up in the pool
+
+
+def test_noalloc_full_sweeps_beyond_its_layer_flags(mdp):
+    """A model with more time layers than the scratch has layer flags for
+    runs full Jacobi sweeps: with an explicit max_sweeps it returns the same
+    values, policy, sweep count and residual as mdp_solve; without one the
+    default nt + 1 sweeps exceed the scratch and are refused."""
+    env = inputs.make_env(nx=2, ny=3, nt=4100, K=1, N=8, L=7, sigma=(0.3,), seed=9,
+                          amplitude=0.5, n_headings=4, n_speeds=1, r_term=2.0)
+    model = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32))
+    with pytest.raises(mdp.MdpError) as ei:
+        mdp.mdp_solve_noalloc(model, 0)
+    assert ei.value.code == -1 and "4092" in str(ei.value)
+    for ms, tol in ((12, 0.0), (4092, 1e-3)):
+        Vr, pir, sr = mdp.mdp_solve(model, 0, method=mdp.MDP_SOLVE_JACOBI_FULL, tol=tol, max_sweeps=ms)
+        for _ in range(2):
+            V, pi, st = mdp.mdp_solve_noalloc(model, 0, tol=tol, max_sweeps=ms)
+            assert (st.sweeps, st.residual) == (sr.sweeps, sr.residual)
+            _check_same(V, pi, Vr, pir)
