@@ -284,29 +284,31 @@ def aggregate(t_ms, samples, backups, world, device):
     return float(tmax[0]), float(tsum[0]), float(tsum[1])
 
 
-def run_batch(args):
+def batch_compare(steps, warmup):
     """64 uneven MDPs solved exactly (tol = 0): one batched run (persistent
     build launches + the batched layered pass, CUDA graph) against the same 64
     built and solved one after another with the plain calls -- the plain
     method (Jacobi sweeps to tol = 0, the same values bit for bit) and, to
-    separate the batching gain from the schedule, the plain layered pass."""
+    separate the batching gain from the schedule, the plain layered pass.
+    Returns the result line (dict)."""
     import torch
-    torch.cuda.set_device(0)
     from paper_2109_00857_gb300 import inputs, mdp
-    mdp.load()
     envs = [inputs.batch_member(i) for i in range(64)]
     denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
     b = mdp.Batch(denvs, tol=0.0)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run()
     torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         sweeps, ms = b.run()
         times.append(time.perf_counter() - t0)
     batch_s = statistics.median(times)
     samples = sum(e.samples() - e.N * e.A * e.Nc for e in envs)   # the last layer needs no sampling
+
     # the plain path: build + solve each member in turn
     def plain(method):
         for d, e in zip(denvs, envs):
@@ -318,7 +320,7 @@ def run_batch(args):
         plain(method)
         torch.cuda.synchronize()
         pt = []
-        for _ in range(max(1, args.steps // 2)):
+        for _ in range(max(1, steps // 2)):
             t0 = time.perf_counter()
             plain(method)
             torch.cuda.synchronize()
@@ -326,9 +328,11 @@ def run_batch(args):
         return statistics.median(pt)
     plain_s = timed(mdp.MDP_SOLVE_JACOBI)
     layered_s = timed(mdp.MDP_SOLVE_LAYERED)
-    line = {"metric": "batched build+solve to the exact fixed point, solves/s (64 uneven MDPs)",
+    clocks = clk.stop()
+    b.close()
+    return {"metric": "batched build+solve to the exact fixed point, solves/s (64 uneven MDPs)",
             "value": 64 / batch_s,
-            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": batch_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 batch members: side U{40..160}, nt U{20..80}, K U{2..6}, "
@@ -340,9 +344,15 @@ def run_batch(args):
             "sequential_layered": {"solves_per_s": 64 / layered_s, "ms": layered_s * 1e3,
                                    "solve": "mdp_solve layered"},
             "speedup_vs_sequential": plain_s / batch_s,
-            "speedup_vs_sequential_layered": layered_s / batch_s}
-    print(json.dumps(line), flush=True)
-    b.close()
+            "speedup_vs_sequential_layered": layered_s / batch_s, "clocks": clocks}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import mdp
+    mdp.load()
+    print(json.dumps(batch_compare(args.steps, args.warmup)), flush=True)
 
 
 def run_cube(args):
@@ -447,17 +457,22 @@ def run_cube(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """Poisson replanning requests against the server (8 slots, 120 GB budget)
-    and against one-at-a-time processing (1 slot), same request stream."""
+def serve_compare(rates, seconds, n_envs=24):
+    """Poisson replanning requests (Sec. V) against the server -- 8 slots and
+    1 slot, 120 GB budget -- and against one-at-a-time plain calls (build +
+    solve + V and policy to the host, in arrival order) with the plain Jacobi
+    schedule and with the plain layered pass; the same request stream for all
+    four.  Requests draw one of n_envs resident environments (sides U{30..120},
+    nt U{20..60}, K U{1..6}), a start and 2x2 target, sigma x U[0.5, 1.5], a
+    seed, N U{500..2000} and an objective.  Returns the result line (dict)."""
+    import copy
+    import dataclasses
     import torch
-    torch.cuda.set_device(0)
     from paper_2109_00857_gb300 import inputs, mdp
-    mdp.load()
     rng = np.random.default_rng(5500)
-    sides = [30, 48, 66, 84, 102, 120]
     envs = []
-    for k, side in enumerate(sides):
+    for k in range(n_envs):
+        side = int(rng.integers(30, 121))
         nt = int(rng.integers(20, 61))
         K = int(rng.integers(1, 7))
         envs.append(inputs.make_env(nx=side, ny=side, nt=nt, K=K, N=1000, L=21,
@@ -466,7 +481,7 @@ def run_serve(args):
                                     square=max(4, side // 10), with_gbar=True))
     denvs = [mdp.DeviceEnv(e, mdp.MDP_FP32) for e in envs]
 
-    def requests(rate, seconds, seed):
+    def requests(rate, seed):
         r = np.random.default_rng(seed)
         t, out = 0.0, []
         while True:
@@ -474,17 +489,22 @@ def run_serve(args):
             if t > seconds:
                 return out
             k = int(r.integers(0, len(envs)))
-            side = sides[k]
+            side = envs[k].nx
             out.append((t, k, dict(start=(int(r.integers(0, side)), int(r.integers(0, side))),
                                    target=(int(r.integers(0, side - 2)), int(r.integers(0, side - 2))),
                                    sigma_scale=float(r.uniform(0.5, 1.5)), seed=int(r.integers(1, 1 << 30)),
                                    N=int(r.integers(500, 2001)), objective=int(r.integers(0, 3)))))
 
-    def run(slots, reqs):
+    def summary(lat, wall):
+        lat = np.asarray(lat)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "solves_per_s": len(lat) / wall, "requests": len(lat), "wall_s": wall}
+
+    def served(slots, reqs):
         srv = mdp.Server(120 << 30, slots)
         ids = [srv.register(d) for d in denvs]
-        w = srv.submit(ids[0], start=(1, 1), target=(5, 5), N=200)   # warm-up
-        srv.poll(w, timeout_ms=120000)
+        for i in ids[:4]:   # warm-up
+            srv.poll(srv.submit(i, start=(1, 1), target=(5, 5), N=200), timeout_ms=120000)
         t0 = time.perf_counter()
         tickets = []
         for (ta, k, kw) in reqs:
@@ -496,20 +516,15 @@ def run_serve(args):
         for t in tickets:
             res, _, _ = srv.poll(t, timeout_ms=600000)
             if res.status != 0:
-                raise RuntimeError(f"request failed with status {res.status}: {srv.error(t) if hasattr(srv, 'error') else ''}")
+                raise RuntimeError(f"request failed with status {res.status}")
             lat.append(res.latency_ms)
         wall = time.perf_counter() - t0
         srv.close()
-        lat = np.array(lat)
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "solves_per_s": len(lat) / wall, "requests": len(lat), "wall_s": wall}
+        return summary(lat, wall)
 
-    def plain(reqs):
-        """The plain method one request at a time, in arrival order: mdp_build +
-        mdp_solve (Jacobi to tol = 0, the same fixed point the server returns)
-        + V and policy to the host; latency = completion - arrival."""
-        import copy
-        import dataclasses
+    def plain(reqs, method):
+        """The plain calls one request at a time, in arrival order;
+        latency = completion - arrival."""
         stream = torch.cuda.Stream()
         t0 = time.perf_counter()
         lat = []
@@ -526,35 +541,87 @@ def run_serve(args):
             tgt[tj:tj + 2, ti:ti + 2] = 1
             d.target = tgt
             m = mdp.mdp_build(d, objs=(kw["objective"],), stream=stream)
-            V, pi, st = mdp.mdp_solve(m, 0, tol=0.0, stream=stream)
+            V, pi, st = mdp.mdp_solve(m, 0, method=method, tol=0.0, stream=stream)
             V.cpu(), pi.cpu()
             m.free()
             lat.append(time.perf_counter() - t0 - ta)
         wall = time.perf_counter() - t0
-        lat = np.array(lat) * 1e3
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "solves_per_s": len(lat) / wall, "requests": len(lat), "wall_s": wall}
+        return summary(np.array(lat) * 1e3, wall)
 
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
     rows = []
-    for rate in [float(x) for x in args.serve_rates.split(",")]:
-        reqs = requests(rate, args.serve_seconds, int(rate) + 1)
-        served = run(8, reqs)
-        single = run(1, reqs)
-        base = plain(reqs)
-        rows.append({"rate_per_s": rate, "served_8_slots": served, "server_1_slot": single,
-                     "plain_one_at_a_time": base,
-                     "served_beats_plain": bool(served["p99_ms"] < base["p99_ms"] and
-                                                served["solves_per_s"] >= 0.99 * base["solves_per_s"])})
+    for rate in rates:
+        reqs = requests(rate, int(rate) + 1)
+        s8 = served(8, reqs)
+        s1 = served(1, reqs)
+        pj = plain(reqs, mdp.MDP_SOLVE_JACOBI)
+        pl = plain(reqs, mdp.MDP_SOLVE_LAYERED)
+        rows.append({"rate_per_s": rate, "served_8_slots": s8, "server_1_slot": s1,
+                     "plain_jacobi": pj, "plain_layered": pl,
+                     "served_beats_plain": bool(s8["p99_ms"] < min(pj["p99_ms"], pl["p99_ms"]) and
+                                                s8["solves_per_s"] >= 0.99 * max(pj["solves_per_s"],
+                                                                                 pl["solves_per_s"]))})
+    clocks = clk.stop()
     top = rows[-1]["served_8_slots"]
-    line = {"metric": "replan p50/p99 ms", "value": top["p99_ms"], "unit": "ms (p99 at the highest rate)",
+    return {"metric": "replan p50/p99 ms", "value": top["p99_ms"], "unit": "ms (p99 at the highest rate)",
             "n_gpus": 1, "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"Poisson replanning requests, {args.serve_seconds:.0f} s per rate, "
-                                   "grids 30..120, nt 20..60, K<=6, N 500..2000, sigma x0.5..1.5, "
-                                   "120 GB budget",
-                       "baseline": "plain mdp_build + mdp_solve (Jacobi, tol 0) one request at a time"},
-            "rates": rows}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": f"Poisson replanning requests, {seconds:.0f} s per rate and arm, "
+                                   f"{n_envs} resident environments: sides U{{30..120}}, nt U{{20..60}}, "
+                                   "K U{1..6}; N U{500..2000}, sigma x U[0.5, 1.5], 120 GB budget",
+                       "baseline": "plain mdp_build + mdp_solve one request at a time (Jacobi and layered)"},
+            "rates": rows, "clocks": clocks}
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2109_00857_gb300 import mdp
+    mdp.load()
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    print(json.dumps(serve_compare(rates, args.serve_seconds)), flush=True)
+
+
+def plain_workload(name, steps, warmup):
+    """Build + fused Jacobi solve of one configuration (tiny, energy), inputs
+    resident in HBM: transitions/s with its own clock record."""
+    import torch
+    from paper_2109_00857_gb300 import mdp
+    env = workload(name)
+    objs = env.objectives
+    denv = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    stream = torch.cuda.Stream()
+    Vb = [torch.empty(env.nS + 1, device="cuda") for _ in objs]
+    Pb = [torch.empty(env.nS, dtype=torch.int16, device="cuda") for _ in objs]
+
+    def step():
+        m = mdp.mdp_build(denv, objs=objs, stream=stream)
+        info = m.info()
+        _, _, sts = mdp.mdp_solve_multi(m, tuple(range(len(objs))), tol=0.0, V=Vb, policy=Pb, stream=stream)
+        m.free()
+        return info, sts
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    samples, bms, sms = 0, [], []
+    e0.record(stream)
+    for _ in range(steps):
+        info, sts = step()
+        samples += info.samples
+        bms.append(info.build_ms)
+        sms.append(sts[0].solve_ms)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_ms = e0.elapsed_time(e1)
+    return {"workload": env.name, "value": samples / (t_ms / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": t_ms / steps, "phase_ms": {"build": statistics.mean(bms), "solve": statistics.mean(sms)},
+            "objectives": list(objs), "solve": "jacobi (fused objectives), tol = 0", "clocks": clocks}
 
 
 def main():
@@ -564,8 +631,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve", "cube"])
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-rates", default="20,50,100,200,400")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rates", default="20,100,200,400")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tiny / energy / batch / serving measurements of the default line")
     ap.add_argument("--solve", default="jacobi", choices=["jacobi", "jacobi_full", "layered"])
     ap.add_argument("--separate", action="store_true",
                     help="solve the objectives one after another instead of one fused solve")
@@ -794,6 +863,28 @@ def main():
         line["e2e"] = {"value": samples / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
                        "wall_s": time.perf_counter() - t0}
+
+    # the same model solved by the layered pass (backward induction over the
+    # time layers, the Jacobi fixed point bit for bit), outside the timed step
+    m = mdp.mdp_build(denv, objs=objs, opts=opts, stream=stream)
+    lay = []
+    for _ in range(3):
+        _, _, sts = mdp.mdp_solve_multi(m, tuple(range(len(objs))), method=mdp.MDP_SOLVE_LAYERED, V=Vbuf,
+                                        policy=Pbuf, stream=stream)
+        lay.append(sts[0].solve_ms)
+    m.free()
+    line["layered_solve"] = {"ms": min(lay), "objectives": len(objs),
+                             "bellman_updates_per_s": env.nS * env.A * len(objs) / (min(lay) / 1e3),
+                             "achieved_gbs": bellman_bytes_per_sweep(info, env.nS, len(objs)) / (min(lay) / 1e3) / 1e9,
+                             "note": "one pass over P (nt launches): the same values and policy as the Jacobi solve"}
+
+    # the other workloads of the metric, each with its own clock record
+    if world == 1 and not args.no_extras and args.config == "large":
+        rates = [float(x) for x in args.serve_rates.split(",")]
+        line["tiny"] = plain_workload("tiny", 20, 5)
+        line["energy"] = plain_workload("energy", 5, 2)
+        line["batch"] = batch_compare(5, 2)
+        line["serve"] = serve_compare(rates, args.serve_seconds)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(env, args.cpu_seconds)

@@ -368,9 +368,19 @@ void mdp_batch_free(mdp_batch b);
 /* -------------------------------------------------------------- serving --
  * Replanning server (on-board re-planning, Sec. V): environment fields stay
  * resident on the device; requests carry a new start/target, a coefficient
- * variance scale, a seed and N.  Requests are admitted while the HBM budget and
- * free slots allow, run concurrently on per-slot streams (continuous batching),
- * and retire independently. */
+ * variance scale, a seed and N.  Requests are admitted in arrival order while
+ * the HBM budget and free slots allow, run concurrently on per-slot streams
+ * (continuous batching), and retire independently.
+ * Memory: each request is charged, at admission, an upper bound of all the
+ * device memory its build and solve can hold with an entry pool of a given
+ * size, and its build never allocates a larger pool; the size comes from the
+ * widths the environment's earlier requests needed.  A request whose slices
+ * need more columns is charged again for the exact need and goes back to the
+ * head of the queue (or ends with MDP_ERR_BUDGET if that exceeds the whole
+ * budget), so the requests in flight never hold more than the budget.
+ * Scheduling: a request runs on a stream whose priority follows its age among
+ * the requests in flight (the oldest highest), so the GPU serves them close to
+ * first come, first served while later ones fill the gaps. */
 typedef struct mdp_server_t *mdp_server;
 
 typedef struct {
@@ -404,7 +414,8 @@ typedef struct {
   int32_t sweeps;                /* Jacobi sweeps (1 for the layered pass) */
   double latency_ms;             /* submit -> completion (host clock) */
   double queue_ms;               /* submit -> admission */
-  int64_t device_bytes;          /* memory the request held */
+  int64_t device_bytes;          /* device memory the request was charged (an upper bound of
+                                    what it held) */
 } mdp_result;
 
 /* hbm_budget_bytes: device memory the server may hold for requests;
@@ -426,6 +437,20 @@ mdp_status mdp_serve_destroy(mdp_server s);
 
 const char *mdp_last_error(void);
 const char *mdp_version(void);
+
+/* Failure injection for tests (the library's own test suite; not for
+ * production use).  Every device-side wait of the Bellman sweeps is bounded:
+ * after a limit of clock cycles it gives up, the kernel drains its copies in
+ * flight, records the failure in the call's status word and returns, and the
+ * call reports MDP_ERR_TIMEOUT with the device context still usable.
+ *   MDP_TEST_WAIT_NEVER_COMPLETES: the next mdp_solve / mdp_solve_multi's first
+ *     round of the one-state-per-slice sweep expects `value` bytes (a multiple
+ *     of 16, <= 1 MiB) that are never copied, so that wait runs out (one shot);
+ *   MDP_TEST_WAIT_LIMIT_CYCLES: the limit of those waits (0 = the default,
+ *     about 2 s).
+ * Returns MDP_ERR_ARG for other keys or values.  The paper has no counterpart. */
+enum { MDP_TEST_WAIT_NEVER_COMPLETES = 1, MDP_TEST_WAIT_LIMIT_CYCLES = 2 };
+mdp_status mdp_test_inject(int32_t what, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,7 @@
 // launch sequencing and status read-back for build, export, solve and the
 // standalone coefficient sampler.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -227,6 +228,28 @@ void free_model_on_stream(mdp_model_t *m, cudaStream_t st) {
 
 using namespace mdpgb;
 
+namespace mdpgb {
+static std::atomic<long long> g_test_wait_cycles{0};
+static std::atomic<uint32_t> g_test_extra_tx{0};
+void take_test_injection(SolveArgs &a) {
+  a.wait_cycles = g_test_wait_cycles.load();
+  a.test_extra_tx = g_test_extra_tx.exchange(0u);
+}
+}  // namespace mdpgb
+
+extern "C" mdp_status mdp_test_inject(int32_t what, int64_t value) {
+  if (what == MDP_TEST_WAIT_NEVER_COMPLETES && value >= 0 && value <= (1 << 20) && (value % 16) == 0) {
+    g_test_extra_tx.store((uint32_t)value);
+    return MDP_OK;
+  }
+  if (what == MDP_TEST_WAIT_LIMIT_CYCLES && value >= 0) {
+    g_test_wait_cycles.store((long long)value);
+    return MDP_OK;
+  }
+  set_error("invalid argument: mdp_test_inject(what, value)");
+  return MDP_ERR_ARG;
+}
+
 extern "C" const char *mdp_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *mdp_version(void) { return "mdp_gb300 1.0 (sm_103a)"; }
 
@@ -264,7 +287,7 @@ namespace mdpgb {
 // (the batched build launches them itself).
 mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
                       int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,
-                      void *stream, mdp_model *out, BuildHook *hook) {
+                      void *stream, mdp_model *out, BuildHook *hook, BuildLimits *lim) {
   if (out) *out = nullptr;
   mdp_status s = check_device();
   if (s != MDP_OK) return s;
@@ -413,6 +436,7 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
     return c < 1 ? (uint64_t)1 : c;
   };
   uint64_t cap_cols = (hook && hook->pool_cols) ? hook->pool_cols : pool_cols_for(kPoolGuess);
+  if (lim && lim->pool_cols) cap_cols = lim->pool_cols;   // the caller's pool size (and limit)
   TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
   TRY(dev_alloc((void **)&m->slice_off, sizeof(uint32_t) * (size_t)m->n_slices, st));
   TRY(dev_alloc((void **)&m->slice_w, (size_t)m->n_slices, st));
@@ -479,11 +503,29 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
     cudaEventRecord(ev1, st);
     TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    const uint64_t worst = pool_cols_for(Wmax);
-    if (c[CNT_POOL_FULL] == 0 || attempt > 0 || worst <= cap_cols) break;
-    // rebuild once with the worst-case pool (counters reset, sampled Y kept)
+    if (c[CNT_POOL_FULL] == 0 || attempt > 0) break;
+    // The pool ran out.  The column counter holds every slice's width even
+    // for the slices that did not fit, i.e. exactly the columns the build
+    // needs: rebuild once with a pool of that size (counters reset, sampled
+    // Y kept) -- unless the caller fixed the pool size, then report the need.
+    const uint64_t need = c[CNT_POOL_COLS];
+    if (lim && lim->pool_cols) {
+      lim->pool_cols_needed = need;
+      char buf[160];
+      snprintf(buf, sizeof buf, "the entry pool needs %llu columns, above the %llu allowed",
+               (unsigned long long)need, (unsigned long long)lim->pool_cols);
+      set_error(buf);
+      if (Yown) dev_free(Yown, st);
+      if (sig_d) dev_free(sig_d, st);
+      if (defer) dev_free(defer, st);
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      cudaEventDestroy(evk);
+      return fail(MDP_ERR_BUDGET);
+    }
+    if (need > budget_cols) break;   // does not fit the device: reported as MDP_ERR_OOM below
     dev_free(m->pool, st);
-    cap_cols = worst;
+    cap_cols = std::max<uint64_t>(need, 1);
     TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
     TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_CAPPED, st));
     TRY(cudaMemsetAsync(m->cnt + CNT_WORK, 0, sizeof(unsigned long long) * (CNT_N - CNT_WORK), st));
@@ -664,6 +706,7 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   a.err = reinterpret_cast<int *>(sd + 2);
   a.nt = m->nt;
   a.pool_ordered = m->pool_ordered;
+  take_test_injection(a);
   if (active) {
     a.work = reinterpret_cast<unsigned long long *>(sd + blk * n);
     a.lflags = reinterpret_cast<uint8_t *>(sd + blk * n + max_sweeps);

@@ -136,11 +136,11 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t par
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait_suspend(bar, parity)) {
-    if (clock64() - t0 > 4000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -797,6 +797,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
   }
   __syncthreads();
   const uint32_t full0 = smem_u32(&hdr->full[0]), empty0 = smem_u32(&hdr->empty[0]);
+  const long long wait_limit = a.wait_cycles > 0 ? a.wait_cycles : 4000000000LL;   // ~2 s
   const uint32_t slots0 = smem_u32(slots);
 
   if (warp == kWsCons) {
@@ -829,7 +830,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
     int slot = 0;
     uint32_t ph = 0;   // phase parity of the slot's current round
     for (int r = 0;; ++r) {
-      if (r >= kWsSlots && !mbar_wait_suspend(empty0 + 8u * (uint32_t)slot, ph ^ 1u)) {
+      if (r >= kWsSlots && !mbar_wait_suspend(empty0 + 8u * (uint32_t)slot, ph ^ 1u, wait_limit)) {
         if (lane == 0) atomicOr(a.err, 1);
         failed = true;
         break;
@@ -858,7 +859,10 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
         hdr->round[slot] = make_int2((int)sl, n);
         if (n > 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the slot's earlier reads
-          mbar_expect_tx(fb, (uint32_t)(tot + NO * n * kRB));
+          // (a.test_extra_tx: bytes that never arrive, on the first round of CTA 0,
+          // so that a bounded wait runs out -- failure injection for tests)
+          const uint32_t extra = (r == 0 && blockIdx.x == 0) ? a.test_extra_tx : 0u;
+          mbar_expect_tx(fb, (uint32_t)(tot + NO * n * kRB) + extra);
         } else {
           mbar_arrive(fb);   // no more rounds: the consumers stop here
         }
@@ -899,7 +903,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
       for (int i = 0; i < kWsSlots; ++i) {
         slot = (slot + kWsSlots - 1) % kWsSlots;   // the last rounds, newest first
         if (slot == kWsSlots - 1) ph ^= 1u;
-        mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph);
+        mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph, wait_limit);
       }
     }
   } else {
@@ -926,7 +930,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
     int slot = 0;
     uint32_t ph = 0;
     for (;;) {
-      if (!mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph)) {
+      if (!mbar_wait_suspend(full0 + 8u * (uint32_t)slot, ph, wait_limit)) {
         if (lane == 0) atomicOr(a.err, 1);
         break;
       }
@@ -946,7 +950,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
         const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb + kRBytes + sd.x) + lane;
         const int sn = (s + Nc <= nS) ? s + Nc : nS;
         const Pk *Vn = v.in + sn;
-#pragma unroll 4
+#pragma unroll 2
         for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
           const uint32_t w = ent[kk * 32];
           const Pk g = Vn[(int)(int16_t)(w & 0xFFFFu)];
@@ -1282,10 +1286,13 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
 }
 
 // Warp-specialized sweep: per slot the R rows of up to 32 slices and the
-// entry bytes of a round; three slots of ~44 KB (FP32, three objectives) keep
-// about two rounds of copies in flight while one is read and leave the rest of
-// the SM's 256 KB to L1.  A slot always holds the widest slice.
-constexpr size_t kWsSmem = 132 * 1024;
+// entry bytes of a round; three slots of ~53 KB (FP32, three objectives) keep
+// two full rounds of copies in flight while one is read and leave ~60 KB of
+// the SM's 256 KB to L1 for the V(s') window.  A slot always holds the widest
+// slice.  (Measured on the large instance: 132 KB 114 ms, 160 KB 104 ms,
+// 190 KB 104 ms, 215 KB 107 ms per fused solve; four or five slots in the
+// same memory make shorter rounds and are slower.)
+constexpr size_t kWsSmem = 160 * 1024;
 
 template <typename RT, int NO>
 static int ws_entry_bytes(int wcap) {

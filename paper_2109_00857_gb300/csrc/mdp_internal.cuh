@@ -207,7 +207,13 @@ struct SolveArgs {
   unsigned long long *work = nullptr;   // [max_sweeps] slices computed per sweep (or nullptr)
   int32_t nt = 0;
   int32_t pool_ordered = 0;   // the model's pool_ordered: a run of slices is one contiguous copy
+  long long wait_cycles = 0;  // bounded waits give up after this many clock cycles (0: ~2 s)
+  uint32_t test_extra_tx = 0; // failure injection (tests): bytes one wait expects that never arrive
 };
+// Failure injection for tests, set on the host by mdp_test_inject: the next
+// solve's first round expects this many bytes too many (one shot), and the
+// bounded waits' limit in clock cycles (0: the default).
+void take_test_injection(SolveArgs &a);
 // batched solve (FP32): one Jacobi sweep over many models per launch
 struct BatchSolveItem {
   SolveArgs a;                // the model (R of the objective being solved)
@@ -287,9 +293,16 @@ struct BuildHook {
   uint32_t *defer = nullptr;  // out: deferred-slice list (owned by the caller now)
   int threads = 256;          // out: CTA size of the full-window kernel
 };
+// A caller that accounts device memory (the server) fixes the entry pool's
+// size: the build then never allocates a larger pool, and if the slices need
+// more columns it returns MDP_ERR_BUDGET with the exact need.
+struct BuildLimits {
+  uint64_t pool_cols = 0;          // in: pool columns to allocate (0: the build's own guess)
+  uint64_t pool_cols_needed = 0;   // out (MDP_ERR_BUDGET): the columns the slices need
+};
 mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
                       int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,
-                      void *stream, mdp_model *out, BuildHook *hook);
+                      void *stream, mdp_model *out, BuildHook *hook, BuildLimits *lim = nullptr);
 
 // Frees a model's device memory in the order of `st` (no device-wide sync):
 // for callers that know the model's work was issued on that stream.

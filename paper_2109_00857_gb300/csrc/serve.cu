@@ -13,6 +13,20 @@
 // Requests admitted while others run overlap with them on the GPU (continuous
 // batching); each retires on its own, copies V and the policy to host memory
 // and releases its device memory.
+//
+// Memory accounting is a hard bound: a request is charged, at admission, the
+// most device memory its build and solve can hold with an entry pool of a
+// given size (every array the calls allocate, as if all were live at once),
+// and the build is held to that pool size.  The size comes from the widths
+// the environment's earlier requests needed; if a request's slices need more
+// columns the build stops before allocating them and reports the exact need,
+// and the request goes back to the head of the queue charged for that need.
+//
+// Scheduling: requests run on CUDA streams of graded priority by admission
+// order -- the oldest request in flight on the highest priority -- so the GPU
+// serves them close to first come, first served while later requests fill
+// the gaps the earlier ones leave (host round trips, short launches).
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -44,13 +58,16 @@ struct EnvEntry {
   int K = 0, L = 0;
   void *vbar = nullptr, *modes = nullptr, *gbar = nullptr;
   uint8_t *obstacle = nullptr;
+  double cols_per_slice = 16.0;   // pool columns per slice to charge the next request for
 };
 
 struct Job {
   uint64_t ticket = 0;
   mdp_request req{};
   Clock::time_point submitted, admitted, finished;
-  int64_t bytes = 0;
+  int64_t bytes = 0;             // charged device memory
+  uint64_t pool_cols = 0;        // entry-pool size the charge covers
+  int level = 0;                 // stream priority level (0 = highest)
   mdp_status status = MDP_ERR_PENDING;
   std::string error;
   int32_t sweeps = 0;
@@ -77,21 +94,54 @@ struct mdp_server_t {
   int64_t in_flight = 0;
   uint64_t next_ticket = 1;
   bool stopping = false;
+  int prio_levels = 1, prio_greatest = 0;   // stream priorities: greatest = numerically lowest
+  std::deque<std::shared_ptr<Job>> running; // admitted requests, in admission order
 };
 
 namespace {
 
-// Device memory a request holds at its peak (the build's first pool guess of
-// 16 columns per slice, rows, R, classes, V pair, policy, coefficients).
-int64_t estimate_bytes(const EnvEntry &e, const mdp_request &r) {
-  const int64_t nt = e.grid.nt - r.start_t;
-  const int64_t nS = (int64_t)e.grid.nx * e.grid.ny * nt;
+// Geometry of a request's model: the remaining horizon's states and slices.
+struct ReqShape {
+  int64_t nt, nS, n_slices, rows_pad, nbins;
+};
+ReqShape req_shape(const EnvEntry &e, const mdp_request &r) {
+  ReqShape g;
+  g.nt = e.grid.nt - r.start_t;
+  g.nS = (int64_t)e.grid.nx * e.grid.ny * g.nt;
   int A = e.actions.n_headings * e.actions.n_speeds, A_pad = 1;
   while (A_pad < A) A_pad <<= 1;
-  const int64_t spw = 32 / A_pad, n_slices = (nS + spw - 1) / spw, rows = n_slices * 32;
-  const int64_t pool = n_slices * 16 * 128;
-  return pool + rows * (1 + 2 + 4) + n_slices * 5 + nS * (1 + 4 + 4 + 2) +
-         nt * r.N * e.K * 4 + (int64_t)e.grid.nx * e.grid.ny + (1 << 20);
+  const int64_t spw = 32 / A_pad;
+  g.n_slices = (g.nS + spw - 1) / spw;
+  g.rows_pad = g.n_slices * 32;
+  const int64_t L = e.L > 0 ? e.L : 255;   // automatic sub-grid: at most 255 cells a side
+  g.nbins = L * L;
+  return g;
+}
+
+// The most device memory a request can hold with an entry pool of pool_cols
+// columns: every allocation of its build (coefficients, pool, slice and row
+// arrays, R, cell classes, offsets, deferred-slice list, the compacted pool and
+// its scan while the first pool is still live), its solve (status words, the
+// Jacobi partner vector and layer flags) and the request's own V and policy,
+// each rounded up to 4 KiB, plus 1 MiB.
+int64_t charge_bytes(const EnvEntry &e, const mdp_request &r, uint64_t pool_cols) {
+  const ReqShape g = req_shape(e, r);
+  auto al = [](int64_t x) { return (x + 4095) & ~(int64_t)4095; };
+  const int64_t max_sweeps = g.nt + 1;
+  int64_t b = 0;
+  b += al(8 * 16) + al(4 * g.nt * r.N * e.K) + al(8 * (e.K + 1)) + al(4 * (2 + 3 * e.K));   // counters, Y, sigma, extremes
+  b += 2 * al((int64_t)pool_cols * 128);                                                      // pool + compacted pool
+  b += al(8 * (g.n_slices + 2) + 8 * (g.n_slices / 1000 + 64));                              // reorder scan
+  b += al(4 * g.n_slices) + al(g.n_slices) + al(g.rows_pad) + al(2 * g.rows_pad) + al(4 * g.rows_pad);
+  b += al(g.nS) + al(4 * g.nbins) + al(4 * g.n_slices);                                        // classes, offsets, defer
+  b += al(8 * (4 + 2 * max_sweeps + (3 * (g.nt + 1) + 7) / 8 + 1));                           // solve status
+  b += 3 * al(4 * (g.nS + 1)) + al(2 * g.nS);                                                  // V, partner, policy
+  b += al((int64_t)e.grid.nx * e.grid.ny);                                                     // target mask
+  return b + (1 << 20);
+}
+
+uint64_t pool_guess(const EnvEntry &e, const mdp_request &r) {
+  return (uint64_t)(e.cols_per_slice * (double)req_shape(e, r).n_slices) + 64;
 }
 
 __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0, int w, int h) {
@@ -102,7 +152,9 @@ __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0
   }
 }
 
-void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
+// Returns true when the request must be charged again for a larger pool
+// (job.pool_cols then holds the exact need).
+bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   const EnvEntry &e = *S->envs[job.req.env_id];
   const mdp_request &r = job.req;
   const int nx = e.grid.nx, ny = e.grid.ny;
@@ -129,11 +181,22 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   env.target = tgt;
   const int32_t obj = r.objective;
   mdp_model m = nullptr;
-  mdp_status s = mdp_build(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m);
+  BuildLimits lim;
+  lim.pool_cols = job.pool_cols;
+  mdp_status s = build_impl(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m, nullptr, &lim);
+  if (s == MDP_ERR_BUDGET && lim.pool_cols_needed > job.pool_cols) {
+    job.pool_cols = lim.pool_cols_needed;
+    cudaStreamSynchronize(st);
+    return true;
+  }
   if (s != MDP_OK) {
     job.status = s;
     job.error = mdp_last_error();
-    return;
+    return false;
+  }
+  {   // the widths this environment's requests need, for the next charges
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->envs[job.req.env_id]->cols_per_slice = std::max(2.0, 1.25 * (double)m->pool_cols / (double)m->n_slices);
   }
   const int64_t nS = m->nS;
   float *V = nullptr;
@@ -145,7 +208,7 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
     job.error = mdp_last_error();
     dev_free(V, st);
     free_model_on_stream(m, st);
-    return;
+    return false;
   }
   mdp_solve_stats ss{};
   // the exact fixed point is reached by one backward pass over the layers
@@ -161,7 +224,7 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
       dev_free(pi, st);
       free_model_on_stream(m, st);
       cudaStreamSynchronize(st);
-      return;
+      return false;
     }
     method |= MDP_SOLVE_WARM;
   }
@@ -190,19 +253,23 @@ void run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   // that would wait for the other slots' work
   free_model_on_stream(m, st);
   cudaStreamSynchronize(st);
+  return false;
 }
 
 void worker_main(mdp_server_t *S) {
   cudaSetDevice(S->device);
-  cudaStream_t st;
-  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  // one stream per priority level; a request runs on the level it got at admission
+  std::vector<cudaStream_t> streams(S->prio_levels);
+  for (int l = 0; l < S->prio_levels; ++l)
+    cudaStreamCreateWithPriority(&streams[l], cudaStreamNonBlocking, S->prio_greatest + l);
   size_t maxc = 0;
   uint8_t *tgt = nullptr;
+  cudaStream_t tst = streams[0];   // the stream the target buffer was last used on
   for (;;) {
     std::shared_ptr<Job> job;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      // FIFO admission: the head waits until its estimate fits the budget
+      // FIFO admission: the head waits until its charge fits the budget
       S->cv_work.wait(lk, [&] {
         return S->stopping || (!S->queue.empty() &&
                                S->bytes_in_use + S->queue.front()->bytes <= (int64_t)S->budget);
@@ -213,33 +280,68 @@ void worker_main(mdp_server_t *S) {
       S->bytes_in_use += job->bytes;
       S->in_flight += 1;
       job->admitted = Clock::now();
+      // priority by age: behind the requests still running
+      job->level = std::min<int>((int)S->running.size(), S->prio_levels - 1);
+      S->running.push_back(job);
     }
+    cudaStream_t st = streams[job->level];
     const EnvEntry &e = *S->envs[job->req.env_id];
     const size_t cells = (size_t)e.grid.nx * e.grid.ny;
+    if (st != tst) {   // the target buffer's last use is ordered before this request's
+      cudaStreamSynchronize(tst);
+      tst = st;
+    }
     if (cells > maxc) {
       dev_free(tgt, st);
       tgt = nullptr;
       if (dev_alloc((void **)&tgt, cells, st) == cudaSuccess) maxc = cells;
     }
+    bool again = false;
     if (!tgt) {
       job->status = MDP_ERR_OOM;
       job->error = "target mask allocation failed";
     } else {
-      run_job(S, *job, st, tgt);
+      again = run_job(S, *job, st, tgt);
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      job->finished = Clock::now();
-      job->done = true;
       S->bytes_in_use -= job->bytes;
       S->in_flight -= 1;
+      for (auto it = S->running.begin(); it != S->running.end(); ++it)
+        if (*it == job) {
+          S->running.erase(it);
+          break;
+        }
+      if (again) {
+        // the slices need a larger pool: charge the exact need and put the
+        // request back at the head of the queue (or refuse it if the whole
+        // budget is too small)
+        job->bytes = charge_bytes(e, job->req, job->pool_cols);
+        if (job->bytes > (int64_t)S->budget) {
+          job->status = MDP_ERR_BUDGET;
+          job->error = "request needs more device memory than the whole HBM budget";
+          again = false;
+        } else if (S->stopping) {
+          job->status = MDP_ERR_CANCELLED;
+          job->error = "server destroyed before the request was admitted";
+          again = false;
+        } else {
+          S->queue.push_front(job);
+        }
+      }
+      if (!again) {
+        job->finished = Clock::now();
+        job->done = true;
+      }
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
-  dev_free(tgt, st);
-  cudaStreamSynchronize(st);
-  cudaStreamDestroy(st);
+  dev_free(tgt, tst);
+  for (cudaStream_t x : streams) {
+    cudaStreamSynchronize(x);
+    cudaStreamDestroy(x);
+  }
 }
 
 }  // namespace
@@ -264,6 +366,11 @@ extern "C" mdp_status mdp_serve_create(size_t hbm_budget_bytes, int32_t max_slot
   cudaGetDevice(&S->device);
   S->budget = hbm_budget_bytes;
   S->slots = max_slots;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess && least > greatest) {
+    S->prio_greatest = greatest;
+    S->prio_levels = std::min(least - greatest + 1, max_slots);
+  }
   for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
   *out = S;
   return MDP_OK;
@@ -348,7 +455,8 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   }
   auto job = std::make_shared<Job>();
   job->req = *req;
-  job->bytes = estimate_bytes(e, *req);
+  job->pool_cols = pool_guess(e, *req);
+  job->bytes = charge_bytes(e, *req, job->pool_cols);
   if (job->bytes > (int64_t)S->budget) {
     set_error("request needs more device memory than the whole HBM budget");
     return MDP_ERR_BUDGET;

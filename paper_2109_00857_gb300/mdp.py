@@ -129,6 +129,7 @@ SIGNATURES = {
     "mdp_serve_stats": (C.c_int, [P, P, P, P]),
     "mdp_serve_destroy": (C.c_int, [P]),
     "mdp_last_error": (C.c_char_p, []),
+    "mdp_test_inject": (C.c_int, [C.c_int32, C.c_int64]),
     "mdp_version": (C.c_char_p, []),
 }
 

@@ -397,3 +397,28 @@ def test_solvers_on_both_sides_of_the_grouped_sweep_width(mdp, scale, width):
     m32 = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), objs=(0, 1, 2))
     for o in range(3):
         solver_parity(mdp, env, m32, o)
+
+
+def test_a_wait_that_runs_out_reports_timeout_and_the_context_stays_usable(mdp):
+    """Failure detection without a GPU fault: every wait of the Bellman sweep is
+    bounded.  A test hook makes the first round of the next solve expect bytes
+    that are never copied (a completion that nothing delivers) and sets a short
+    limit; the wait gives up, the kernel drains and returns, the call reports
+    MDP_ERR_TIMEOUT, and the next solve on the same context gives the same
+    values and policy as before."""
+    env = inputs.energy(nx=20, ny=18, nt=5, N=200)
+    model = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), objs=env.objectives)
+    V0, pi0, _ = mdp.mdp_solve(model, 0, tol=0.0)
+    V0, pi0 = V0.cpu().numpy(), pi0.cpu().numpy()
+    lib = mdp.load()
+    assert lib.mdp_test_inject(7, 0) == -1 and lib.mdp_test_inject(1, 8) == -1
+    assert lib.mdp_test_inject(2, 2_000_000) == 0    # about 1 ms at the GPU's clock
+    assert lib.mdp_test_inject(1, 1024) == 0
+    try:
+        with pytest.raises(mdp.MdpError) as ei:
+            mdp.mdp_solve(model, 0, tol=0.0)
+        assert ei.value.code == -5 and "bounded" in str(ei.value)
+    finally:
+        lib.mdp_test_inject(2, 0)
+    V1, pi1, st1 = mdp.mdp_solve(model, 0, tol=0.0)
+    assert np.array_equal(V1.cpu().numpy(), V0) and np.array_equal(pi1.cpu().numpy(), pi0)

@@ -85,7 +85,13 @@ def test_result_alone_equals_result_in_a_mix(mdp):
 def test_budget_admission_and_errors(mdp):
     env = _env()
     d = mdp.DeviceEnv(env, mdp.MDP_FP32)
-    s = mdp.Server(64 << 20, 2)     # 64 MiB: this environment's requests fit one at a time
+    probe = mdp.Server(8 << 30, 1)
+    eid = probe.register(d)
+    res, _, _ = probe.poll(probe.submit(eid, start=(1, 1), target=(20, 20), seed=99, N=300), timeout_ms=60000)
+    probe.close()
+    charge = res.device_bytes           # what one such request is charged
+    budget = int(1.5 * charge)          # this environment's requests fit one at a time
+    s = mdp.Server(budget, 2)
     eid = s.register(d)
     with pytest.raises(mdp.MdpError) as ei:
         s.submit(eid + 5, start=(1, 1), target=(3, 3))
@@ -97,7 +103,8 @@ def test_budget_admission_and_errors(mdp):
     peak = 0
     for _ in range(400):
         inflight, queued, used = s.stats()
-        assert used <= 64 << 20
+        assert used <= budget
+        assert inflight <= 1
         peak = max(peak, inflight)
         if inflight == 0 and queued == 0:
             break
@@ -212,3 +219,83 @@ def test_served_request_matches_the_oracle(mdp, t0, objective):
     e = _cut_request_env(env, t0, probe["target"], probe["sigma_scale"], probe["seed"], probe["N"])
     assert V.shape == (e.nS + 1,)
     oracle_end_to_end(mdp, e, objective, V, pi)
+
+
+def _wide_env():
+    """Rows of 50+ successors (strong uniform modes): more entry-pool columns
+    per slice than a first charge assumes."""
+    nt = 3
+    modes = np.stack([np.stack([np.ones((nt, 9, 9)), np.zeros((nt, 9, 9))], -1),
+                      np.stack([np.zeros((nt, 9, 9)), np.ones((nt, 9, 9))], -1)], 1)
+    from conftest import custom_env
+    return custom_env(nx=9, ny=9, nt=nt, K=2, N=3000, L=15, seed=12, sigma=[1.1, 1.0], modes=modes)
+
+
+def _pool_used():
+    """(reset high-water mark, read (used now, high-water mark)) of the
+    device's default memory pool, through the CUDA driver API."""
+    import ctypes as C
+    cu = C.CDLL("libcuda.so.1")
+    dev = C.c_int()
+    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    USED, USED_HIGH = 7, 8   # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
+
+    def reset():
+        zero = C.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, C.byref(zero)) == 0
+
+    def read():
+        a, b = C.c_uint64(), C.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, USED, C.byref(a)) == 0
+        assert cu.cuMemPoolGetAttribute(pool, USED_HIGH, C.byref(b)) == 0
+        return a.value, b.value
+    return reset, read
+
+
+def test_a_request_never_holds_more_device_memory_than_it_was_charged(mdp):
+    """The budget is a hard bound: measured by the device memory pool's
+    high-water mark around each request (one slot, nothing else running), a
+    request's peak stays within the bytes it was charged -- also for an
+    environment whose rows are wider than the first charge assumes (the build
+    stops at the charged pool size, the request is charged again for the exact
+    need and rerun) -- and the result equals a direct build + solve."""
+    import torch
+    reset, read = _pool_used()
+    for env, kw in ((_env(), dict(start=(3, 4), target=(20, 20), seed=5, N=300, objective=1)),
+                    (_wide_env(), dict(start=(4, 4), target=(1, 1), seed=7, N=3000, objective=0))):
+        srv = mdp.Server(8 << 30, 1)
+        eid = srv.register(mdp.DeviceEnv(env, mdp.MDP_FP32))
+        for rep in range(2):   # the second request is charged from the first one's widths
+            torch.cuda.synchronize()
+            used0, _ = read()
+            reset()
+            res, V, pi = srv.poll(srv.submit(eid, **kw), timeout_ms=60000, env_id=eid, want_V=True)
+            assert res.status == 0, mdp.load().mdp_last_error().decode()
+            _, high = read()
+            assert high - used0 <= res.device_bytes, (rep, high - used0, res.device_bytes)
+        srv.close()
+        Vd, pid = _direct(mdp, env, kw["target"], 1.0, kw["seed"], kw["N"], kw.get("objective", 0))
+        assert np.array_equal(V, Vd) and np.array_equal(pi, pid)
+
+
+def test_a_request_that_outgrows_the_budget_is_refused(mdp):
+    """Admitted under its first charge, a request whose slices need a pool
+    beyond the whole budget ends with MDP_ERR_BUDGET instead of allocating it."""
+    env = _wide_env()
+    d = mdp.DeviceEnv(env, mdp.MDP_FP32)
+    kw = dict(start=(4, 4), target=(1, 1), seed=7, N=3000)
+    big = mdp.Server(8 << 30, 1)
+    eid = big.register(d)
+    res, _, _ = big.poll(big.submit(eid, **kw), timeout_ms=60000)
+    assert res.status == 0
+    big.close()
+    need = res.device_bytes                # the charge for the exact pool
+    small = mdp.Server(need - 1, 1)        # admits the first charge, not the second
+    eid = small.register(d)
+    res, _, _ = small.poll(small.submit(eid, **kw), timeout_ms=60000)
+    assert res.status == -7
+    inflight, queued, used = small.stats()
+    assert inflight == 0 and queued == 0 and used == 0
+    small.close()
