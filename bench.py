@@ -436,7 +436,7 @@ def run_cube(args):
                                  else "bellman_kernel", "bound": "hbm", "achieved": bell, "peak": hbm,
                                  "unit": "GB/s", "frac": bell / hbm, "bytes_per_sweep": bpsw,
                                  "ms_per_sweep": sweep_ms, "peak_basis": f"hbm_gbs ({peak_kind})"},
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "tuning": tuning,
             "model": {"nnz": info.nnz, "rows": info.rows, "max_row_nnz": info.max_row_nnz,
                       "device_bytes": info.device_bytes}}
     if not args.no_cpu_baseline:
@@ -633,6 +633,7 @@ def main():
     ap.add_argument("--config", default="large", choices=["tiny", "energy", "large", "batch", "serve", "cube"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rates", default="20,100,200,400")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the tiny / energy / batch / serving measurements of the default line")
     ap.add_argument("--solve", default="jacobi", choices=["jacobi", "jacobi_full", "layered"])
@@ -682,6 +683,9 @@ def main():
     opts = mdp.MdpBuildOpts()
     opts.threads, opts.chunk = args.threads, args.chunk
     rec = {}
+    # launch shapes for this workload class, timed on a calibration cut
+    # (outside the timed region); the timed builds and solves use them
+    tuning = None if args.no_autotune else mdp.mdp_autotune(denv, objs=objs, stream=stream).as_dict()
 
     def step(d=denv):
         m = mdp.mdp_build(d, objs=objs, opts=opts, stream=stream)
@@ -795,7 +799,7 @@ def main():
                          "solve": statistics.mean(solve_ms)},
             "sweeps": sweeps[-1],
             "roofline": dominant, "roofline_build": roof_build, "roofline_bellman": roof_bell,
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "tuning": tuning,
             "model": {"nnz": info.nnz, "rows": info.rows, "max_row_nnz": info.max_row_nnz,
                       "device_bytes": info.device_bytes}}
     if world > 1:

@@ -114,12 +114,15 @@ typedef struct {
 typedef struct {
   int32_t row_cap;         /* max stored successors per row incl. sink; 0 = 64 */
   int32_t no_compact;      /* 1: keep the worst-case entry pool instead of compacting it */
-  int32_t threads;         /* build CTA size for FP32 (multiple of 64); 0 = autotuned */
-  int32_t chunk;           /* realizations staged per pass; 0 = autotuned */
+  int32_t threads;         /* CTA size of the FP32 full-window kernel (multiple of 64, <= 512);
+                              0 = the autotuner's choice for the workload class (see
+                              mdp_autotune) if one was recorded or loaded, else 256 */
+  int32_t chunk;           /* realizations staged per pass by that kernel; 0 = the autotuner's
+                              choice, else 1024 */
   int32_t hist_cap;        /* fine-count table cells (32-bit words) per warp of the
-                              warp-per-slice kernel, <= 6144; 0 = 2048; slices whose
-                              tables need more go to the full-window kernel
-                              (1 sends every sampled slice there) */
+                              warp-per-slice kernel, <= 6144; 0 = the autotuner's choice,
+                              else 2048; slices whose tables need more go to the
+                              full-window kernel (1 sends every sampled slice there) */
 } mdp_build_opts;
 
 typedef struct mdp_model_t *mdp_model;
@@ -333,6 +336,40 @@ mdp_status mdp_rollout(const mdp_env *env, const mdp_grid *grid, const mdp_actio
                        int32_t N, const int16_t *policy, const int32_t *starts_h, int32_t n_starts,
                        const int32_t *objs_h, int32_t n_obj, void *ret, int32_t *steps,
                        int8_t *status, mdp_rollout_summary *summary_h, void *stream);
+
+/* ------------------------------------------------------------ autotuner --
+ * Launch shapes per workload class, chosen by timing candidates (the paper's
+ * authors tuned threads per block by hand for each GPU, Sec. IV-D; here the
+ * library does it).  A class is (actions padded to a power of two, modes, N
+ * and cells rounded to powers of two, objectives, precision).  The shapes:
+ * warps per CTA (4, 8) and fine-table words per warp (1536..4096) of the
+ * warp-per-slice build kernel, the CTA size of the full-window kernel when the
+ * calibration defers slices to it, and the shared memory of the
+ * one-state-per-slice Bellman sweep (132, 160, 190 KiB: its slot size).
+ * No choice changes a count, entry, R, value or policy -- only the speed.
+ * mdp_build, mdp_solve, mdp_solve_multi and the batch use the process-wide
+ * table's entry for a model's class wherever the caller leaves an option 0.
+ *
+ * mdp_autotune times every candidate on a calibration cut of the caller's
+ * environment (its first layers, about 200,000 states; arguments as in
+ * mdp_build), records the fastest in the table and, if json_path is not
+ * NULL, merges it into that JSON file ({"<class>": {"build_warps": ..,
+ * "hist_cap": .., "threads": .., "chunk": .., "sweep_smem_kb": ..}, ...}).
+ * mdp_tuning_load installs a file's entries (MDP_ERR_ARG if it cannot be read
+ * or parsed; entries outside the kernels' limits are skipped). */
+typedef struct {
+  int32_t build_warps, hist_cap, threads, chunk, sweep_smem_kb;
+  double build_kernel_ms;    /* calibration build kernel time with the chosen shapes */
+  double sweep_ms;           /* calibration solve time with the chosen sweep memory */
+  int32_t candidates;        /* configurations timed */
+  int32_t calibration_layers;
+  char key[64];              /* workload class */
+} mdp_tuning;
+
+mdp_status mdp_autotune(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
+                        int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const char *json_path,
+                        void *stream, mdp_tuning *out);
+mdp_status mdp_tuning_load(const char *json_path);
 
 /* ------------------------------------------------------------- batching --
  * Builds and solves n (1..1023) independent MDPs of uneven sizes: one

@@ -32,6 +32,7 @@ UNITS = {
     "batch.cu": [],
     "rollout.cu": [],
     "build3d.cu": [],
+    "tune.cu": [],
     "check_fp64.cu": ["-fmad=false"],
 }
 

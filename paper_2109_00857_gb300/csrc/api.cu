@@ -427,8 +427,11 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   // once with the worst case (every slice row_cap wide).
   const int Wmax = std::min(row_cap, m->nbins + 1);
   const int kPoolGuess = 16;
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
+  // the pool may take at most 60 % of the free device memory; asking the
+  // driver costs a round trip, so only pools above 256 MiB ask
+  size_t free_b = (size_t)1 << 62, total_b = 0;
+  if ((uint64_t)m->n_slices * (uint64_t)std::min(kPoolGuess, Wmax) * 128 > ((uint64_t)256 << 20))
+    cudaMemGetInfo(&free_b, &total_b);
   const uint64_t budget_cols = (uint64_t)(0.6 * (double)free_b) / 128;
   auto pool_cols_for = [&](int width) {
     uint64_t c = (uint64_t)m->n_slices * (uint64_t)std::min(width, Wmax) + 64;
@@ -459,12 +462,17 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.slice_w = m->slice_w; ba.nnz = m->nnz; ba.sinkc = m->sinkc;
   ba.R = m->R; ba.cnt = m->cnt;
   ba.slice_begin = 0; ba.slice_end = m->n_slices;
-  int threads = (opts && opts->threads > 0) ? opts->threads : 256;
+  // launch shapes: the caller's, else the autotuner's for this workload class, else defaults
+  Tuning tun;
+  tuning_lookup(tuning_key(m->A_pad, env->K, N, Nc, n_obj, prec), &tun);
+  m->sweep_smem_kb = tun.sweep_smem_kb;
+  int threads = (opts && opts->threads > 0) ? opts->threads : tun.threads;
   if (threads % 64 != 0 || threads > 512) return fail(arg_fail("threads must be a multiple of 64, <= 512"));
-  int chunk = (opts && opts->chunk > 0) ? opts->chunk : 1024;
+  int chunk = (opts && opts->chunk > 0) ? opts->chunk : tun.chunk;
   if (chunk > N) chunk = N;
   ba.chunk = chunk;
-  int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : 2048;
+  int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : tun.hist_cap;
+  const int build_warps = tun.build_warps;
   if (hist_cap > 6144) return fail(arg_fail("hist_cap must be <= 6144"));
   uint32_t *defer = nullptr;
   if (prec == MDP_FP32) TRY(dev_alloc((void **)&defer, sizeof(uint32_t) * (size_t)m->n_slices, st));
@@ -494,7 +502,7 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
       ++launches;
     } else {
       // warp-per-slice kernel, then the full-window CTA kernel over what it deferred
-      TRY(launch_build_warp(ba, 8, num_sms(), st));
+      TRY(launch_build_warp(ba, build_warps, num_sms(), st));
       BuildArgs bd = ba;
       bd.defer_in = defer;
       TRY(launch_build_fp32(bd, threads, num_sms(), st));
@@ -706,6 +714,7 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   a.err = reinterpret_cast<int *>(sd + 2);
   a.nt = m->nt;
   a.pool_ordered = m->pool_ordered;
+  a.sweep_smem_kb = m->sweep_smem_kb;
   take_test_injection(a);
   if (active) {
     a.work = reinterpret_cast<unsigned long long *>(sd + blk * n);

@@ -236,8 +236,20 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
     free_model_on_stream(cm, b->st);
   }
   cudaStreamSynchronize(b->st);
-  // larger fine tables when more than 0.2% of the slices would be deferred
-  b->cap_bins = (wide * 500 > total_slices) ? 4096 : 2048;
+  // the fine-table capacity the autotuner chose for the members' classes (the
+  // largest), else larger tables when more than 0.2% of the slices would be deferred
+  int tuned_cap = 0;
+  for (int i = 0; i < n; ++i) {
+    const Item &it = b->items[i];
+    const int A = it.desc.actions.n_headings * it.desc.actions.n_speeds;
+    int A_pad = 1;
+    while (A_pad < A) A_pad <<= 1;
+    Tuning t;
+    if (tuning_lookup(tuning_key(A_pad, it.desc.env.K, it.desc.N, (int64_t)it.desc.grid.nx * it.desc.grid.ny, 1,
+                                 MDP_FP32), &t))
+      tuned_cap = std::max(tuned_cap, t.hist_cap);
+  }
+  b->cap_bins = tuned_cap > 0 ? tuned_cap : ((wide * 500 > total_slices) ? 4096 : 2048);
   // ---- set-up of every item through the build path, without launching it
   std::vector<BuildArgs> args(n);
   std::vector<int64_t> prefix(n + 1, 0);

@@ -1295,8 +1295,9 @@ __global__ void finalize_kernel(const unsigned long long *res, int max_sweeps, d
 constexpr size_t kWsSmem = 160 * 1024;
 
 template <typename RT, int NO>
-static int ws_entry_bytes(int wcap) {
-  const long per_slot = (long)((kWsSmem - ws_hdr_bytes() - ws_old_bytes<RT, NO>()) / kWsSlots) - ws_r_bytes<RT>(NO);
+static int ws_entry_bytes(int wcap, int smem_kb) {
+  const size_t budget = smem_kb > 0 ? (size_t)smem_kb * 1024 : kWsSmem;
+  const long per_slot = (long)((budget - ws_hdr_bytes() - ws_old_bytes<RT, NO>()) / kWsSlots) - ws_r_bytes<RT>(NO);
   long e = std::max<long>(per_slot, (long)wcap * 128);
   return (int)(e & ~127L);
 }
@@ -1306,7 +1307,7 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
   pr->dtab_smem = 0;
   if (a.spw == 1) {   // one state per slice: the warp-specialized sweep, any width
     pr->grouped = 2;
-    pr->stage_bytes = ws_entry_bytes<RT, NO>(a.wcap);
+    pr->stage_bytes = ws_entry_bytes<RT, NO>(a.wcap, a.sweep_smem_kb);
     *smem = ws_hdr_bytes() + ws_old_bytes<RT, NO>() + (size_t)kWsSlots * (ws_r_bytes<RT>(NO) + pr->stage_bytes);
     cudaError_t e = allow_max_smem((const void *)bellman_kernel_ws<RT, NO>);
     if (e != cudaSuccess) return e;

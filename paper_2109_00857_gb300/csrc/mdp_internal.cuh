@@ -143,6 +143,7 @@ struct mdp_model_t {
   int device;
   int32_t pool_ordered;       // 1: the pool holds the slices in slice order, back to back
                               // (slice_off[sl + 1] = slice_off[sl] + slice_w[sl])
+  int32_t sweep_smem_kb;      // shared memory of the one-state-per-slice Bellman sweep (0: default)
 };
 
 namespace mdpgb {
@@ -207,9 +208,25 @@ struct SolveArgs {
   unsigned long long *work = nullptr;   // [max_sweeps] slices computed per sweep (or nullptr)
   int32_t nt = 0;
   int32_t pool_ordered = 0;   // the model's pool_ordered: a run of slices is one contiguous copy
+  int32_t sweep_smem_kb = 0;  // shared memory of the one-state-per-slice sweep (0: its default)
   long long wait_cycles = 0;  // bounded waits give up after this many clock cycles (0: ~2 s)
   uint32_t test_extra_tx = 0; // failure injection (tests): bytes one wait expects that never arrive
 };
+// Launch shapes chosen by the autotuner (mdp_autotune) per workload class;
+// every choice gives the same model and values bit for bit.
+struct Tuning {
+  int32_t build_warps = 8;       // warps per CTA of the warp-per-slice build kernel
+  int32_t hist_cap = 2048;       // fine-table words per warp of that kernel
+  int32_t threads = 256;         // CTA size of the full-window build kernel
+  int32_t chunk = 1024;          // realizations staged per pass by that kernel
+  int32_t sweep_smem_kb = 160;   // shared memory of the one-state-per-slice Bellman sweep
+};
+// Workload class of a model: actions (padded), modes, N and cells (rounded
+// to powers of two), objectives and precision.
+std::string tuning_key(int A_pad, int K, int N, int64_t Nc, int n_obj, int precision);
+// The tuned shapes of a class, if the autotuner recorded (or loaded) them.
+bool tuning_lookup(const std::string &key, Tuning *out);
+
 // Failure injection for tests, set on the host by mdp_test_inject: the next
 // solve's first round expects this many bytes too many (one shot), and the
 // bounded waits' limit in clock cycles (0: the default).

@@ -59,6 +59,7 @@ struct EnvEntry {
   void *vbar = nullptr, *modes = nullptr, *gbar = nullptr;
   uint8_t *obstacle = nullptr;
   double cols_per_slice = 16.0;   // pool columns per slice to charge the next request for
+  bool cols_seen = false;         // a request has measured it
 };
 
 struct Job {
@@ -194,9 +195,14 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
     job.error = mdp_last_error();
     return false;
   }
-  {   // the widths this environment's requests need, for the next charges
+  {   // the widest pool per slice this environment's requests have needed (with
+      // 10 % to spare) prices the next ones: widths vary with sigma and N, and
+      // a charge that is too small costs the request a second build
     std::lock_guard<std::mutex> lk(S->mu);
-    S->envs[job.req.env_id]->cols_per_slice = std::max(2.0, 1.25 * (double)m->pool_cols / (double)m->n_slices);
+    double &c = S->envs[job.req.env_id]->cols_per_slice;
+    const double need = 1.1 * (double)m->pool_cols / (double)m->n_slices;
+    if (!S->envs[job.req.env_id]->cols_seen || need > c) c = std::max(2.0, need);
+    S->envs[job.req.env_id]->cols_seen = true;
   }
   const int64_t nS = m->nS;
   float *V = nullptr;
@@ -313,6 +319,8 @@ void worker_main(mdp_server_t *S) {
           break;
         }
       if (again) {
+        const double cps = (double)job->pool_cols / (double)req_shape(e, job->req).n_slices;
+        S->envs[job->req.env_id]->cols_per_slice = std::max(S->envs[job->req.env_id]->cols_per_slice, 1.1 * cps);
         // the slices need a larger pool: charge the exact need and put the
         // request back at the head of the queue (or refuse it if the whole
         // budget is too small)

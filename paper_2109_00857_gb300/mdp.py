@@ -86,6 +86,19 @@ class MdpRolloutSummary(C.Structure):
                 ("mean_steps_target", C.c_double), ("paths", C.c_int64)]
 
 
+class MdpTuning(C.Structure):
+    _fields_ = [("build_warps", C.c_int32), ("hist_cap", C.c_int32), ("threads", C.c_int32),
+                ("chunk", C.c_int32), ("sweep_smem_kb", C.c_int32), ("build_kernel_ms", C.c_double),
+                ("sweep_ms", C.c_double), ("candidates", C.c_int32), ("calibration_layers", C.c_int32),
+                ("key", C.c_char * 64)]
+
+    def as_dict(self):
+        return {"class": self.key.decode(), "build_warps": self.build_warps, "hist_cap": self.hist_cap,
+                "threads": self.threads, "chunk": self.chunk, "sweep_smem_kb": self.sweep_smem_kb,
+                "build_kernel_ms": self.build_kernel_ms, "sweep_ms": self.sweep_ms,
+                "candidates": self.candidates, "calibration_layers": self.calibration_layers}
+
+
 class MdpBatchItem(C.Structure):
     _fields_ = [("env", MdpEnv), ("grid", MdpGrid), ("actions", MdpActions), ("N", C.c_int32),
                 ("subgrid_L", C.c_int32), ("objective", C.c_int32), ("V", P), ("policy", P)]
@@ -130,6 +143,8 @@ SIGNATURES = {
     "mdp_serve_destroy": (C.c_int, [P]),
     "mdp_last_error": (C.c_char_p, []),
     "mdp_test_inject": (C.c_int, [C.c_int32, C.c_int64]),
+    "mdp_autotune": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, C.c_char_p, P, P]),
+    "mdp_tuning_load": (C.c_int, [C.c_char_p]),
     "mdp_version": (C.c_char_p, []),
 }
 
@@ -443,6 +458,26 @@ def mdp_sample_coeffs(nt: int, N: int, K: int, sigma, seed: int, mdp_id: int = 0
     _check(load().mdp_sample_coeffs(nt, N, K, sig.ctypes.data_as(P), seed, mdp_id, precision,
                                     _ptr(Y), _stream(stream)), "mdp_sample_coeffs")
     return Y
+
+
+def mdp_autotune(denv: DeviceEnv, objs: Sequence[int] = (MDP_OBJ_TIME,), N: Optional[int] = None,
+                 subgrid_L: Optional[int] = None, json_path: Optional[str] = None, stream=None) -> MdpTuning:
+    """Times the launch-shape candidates on a calibration cut of denv's
+    environment, records the fastest for its workload class (and in json_path)."""
+    lib = load()
+    e, g, a = denv.c_env(), denv.c_grid(), denv.c_actions()
+    ob = np.ascontiguousarray(objs, dtype=np.int32)
+    out = MdpTuning()
+    N = denv.env.N if N is None else N
+    L = denv.env.L if subgrid_L is None else subgrid_L
+    _check(lib.mdp_autotune(C.byref(e), C.byref(g), C.byref(a), N, L, ob.ctypes.data_as(P), len(ob),
+                            json_path.encode() if json_path else None, _stream(stream), C.byref(out)),
+           "mdp_autotune")
+    return out
+
+
+def mdp_tuning_load(json_path: str):
+    _check(load().mdp_tuning_load(json_path.encode()), "mdp_tuning_load")
 
 
 def mdp_version() -> str:

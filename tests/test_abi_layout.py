@@ -29,6 +29,7 @@ PAIRS = {
     "mdp_batch_item": mdp.MdpBatchItem,
     "mdp_request": mdp.MdpRequest,
     "mdp_result": mdp.MdpResult,
+    "mdp_tuning": mdp.MdpTuning,
 }
 
 
