@@ -410,11 +410,13 @@ void mdp_batch_free(mdp_batch b);
  * (continuous batching), and retire independently.
  * Memory: each request is charged, at admission, an upper bound of all the
  * device memory its build and solve can hold with an entry pool of a given
- * size, and its build never allocates a larger pool; the size comes from the
- * widths the environment's earlier requests needed.  A request whose slices
- * need more columns is charged again for the exact need and goes back to the
- * head of the queue (or ends with MDP_ERR_BUDGET if that exceeds the whole
- * budget), so the requests in flight never hold more than the budget.
+ * size, and its build never allocates a larger pool.  The size is the largest
+ * the slices can need when the budget has room for it, else the widest the
+ * environment's earlier requests needed; after the build the charge drops to
+ * that of the compacted model.  A request whose slices need more columns is
+ * charged again for the exact need and goes back to the head of the queue (or
+ * ends with MDP_ERR_BUDGET if that exceeds the whole budget), so the requests
+ * in flight never hold more than the budget.
  * Scheduling: a request runs on a stream whose priority follows its age among
  * the requests in flight (the oldest highest), so the GPU serves them close to
  * first come, first served while later ones fill the gaps. */

@@ -17,10 +17,14 @@
 // Memory accounting is a hard bound: a request is charged, at admission, the
 // most device memory its build and solve can hold with an entry pool of a
 // given size (every array the calls allocate, as if all were live at once),
-// and the build is held to that pool size.  The size comes from the widths
-// the environment's earlier requests needed; if a request's slices need more
-// columns the build stops before allocating them and reports the exact need,
-// and the request goes back to the head of the queue charged for that need.
+// and the build is held to that pool size.  The size is the largest the
+// slices can need (every slice as wide as the row limit) when the budget has
+// room for it -- the build then never stops for want of columns -- else the
+// widest the environment's earlier requests needed; once the model is built
+// and compacted, the charge drops to that of the columns in use.  If a
+// request's slices need more columns than its pool, the build stops before
+// allocating them and reports the exact need, and the request goes back to
+// the head of the queue charged for that need.
 //
 // Scheduling: requests run on CUDA streams of graded priority by admission
 // order -- the oldest request in flight on the highest priority -- so the GPU
@@ -66,7 +70,8 @@ struct Job {
   uint64_t ticket = 0;
   mdp_request req{};
   Clock::time_point submitted, admitted, finished;
-  int64_t bytes = 0;             // charged device memory
+  int64_t bytes = 0;             // device memory charged now
+  int64_t peak_bytes = 0;        // the largest charge it held (reported)
   uint64_t pool_cols = 0;        // entry-pool size the charge covers
   int level = 0;                 // stream priority level (0 = highest)
   mdp_status status = MDP_ERR_PENDING;
@@ -145,6 +150,14 @@ uint64_t pool_guess(const EnvEntry &e, const mdp_request &r) {
   return (uint64_t)(e.cols_per_slice * (double)req_shape(e, r).n_slices) + 64;
 }
 
+// The largest pool the request's slices can need (every slice as wide as the
+// row limit): charged when the budget has room, so the build never stops for
+// want of columns; the charge drops to the compacted model once it is built.
+uint64_t pool_worst(const EnvEntry &e, const mdp_request &r) {
+  const ReqShape g = req_shape(e, r);
+  return (uint64_t)g.n_slices * (uint64_t)std::min<int64_t>(64, g.nbins + 1) + 64;
+}
+
 __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0, int w, int h) {
   const int n = nx * ny;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
@@ -195,6 +208,16 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
     job.error = mdp_last_error();
     return false;
   }
+  {   // the model is compacted: the request now holds at most the charge of a
+      // pool of the columns in use (the rest of its charge goes back)
+    std::lock_guard<std::mutex> lk(S->mu);
+    const int64_t now = charge_bytes(e, job.req, std::max<uint64_t>(m->pool_cols, 1));
+    if (now < job.bytes) {
+      S->bytes_in_use -= job.bytes - now;
+      job.bytes = now;
+    }
+  }
+  S->cv_work.notify_all();
   {   // the widest pool per slice this environment's requests have needed (with
       // 10 % to spare) prices the next ones: widths vary with sigma and N, and
       // a charge that is too small costs the request a second build
@@ -325,6 +348,7 @@ void worker_main(mdp_server_t *S) {
         // request back at the head of the queue (or refuse it if the whole
         // budget is too small)
         job->bytes = charge_bytes(e, job->req, job->pool_cols);
+        job->peak_bytes = std::max(job->peak_bytes, job->bytes);
         if (job->bytes > (int64_t)S->budget) {
           job->status = MDP_ERR_BUDGET;
           job->error = "request needs more device memory than the whole HBM budget";
@@ -463,8 +487,13 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   }
   auto job = std::make_shared<Job>();
   job->req = *req;
-  job->pool_cols = pool_guess(e, *req);
+  job->pool_cols = pool_worst(e, *req);
   job->bytes = charge_bytes(e, *req, job->pool_cols);
+  if (job->bytes > (int64_t)S->budget) {   // too much for the budget: the widths seen so far
+    job->pool_cols = pool_guess(e, *req);
+    job->bytes = charge_bytes(e, *req, job->pool_cols);
+  }
+  job->peak_bytes = job->bytes;
   if (job->bytes > (int64_t)S->budget) {
     set_error("request needs more device memory than the whole HBM budget");
     return MDP_ERR_BUDGET;
@@ -501,7 +530,7 @@ extern "C" mdp_status mdp_serve_poll(mdp_server S, uint64_t ticket, int32_t time
   out->sweeps = job->sweeps;
   out->latency_ms = ms_between(job->submitted, job->finished);
   out->queue_ms = ms_between(job->submitted, job->admitted);
-  out->device_bytes = job->bytes;
+  out->device_bytes = job->peak_bytes;
   if (job->status == MDP_OK) {
     if (V_h) memcpy(V_h, job->V.data(), sizeof(float) * job->V.size());
     if (pi_h) memcpy(pi_h, job->pi.data(), sizeof(int16_t) * job->pi.size());
