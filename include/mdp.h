@@ -52,7 +52,8 @@ typedef enum {
   MDP_ERR_ARG = -1,               /* invalid argument (message says which) */
   MDP_ERR_OOM = -2,               /* device allocation failed or pool capacity hit */
   MDP_ERR_SUBGRID_OVERFLOW = -3,  /* a landing fell outside the neighbouring sub-grid */
-  MDP_ERR_ELL_OVERFLOW = -4,      /* a row had more successors than the row cap */
+  MDP_ERR_ELL_OVERFLOW = -4,      /* a row had more successors than the row cap (batched
+                                     builds and 3-D builds, which keep no spill area) */
   MDP_ERR_TIMEOUT = -5,           /* a bounded wait expired */
   MDP_ERR_CUDA = -6,              /* a CUDA runtime error (message has the CUDA string) */
   MDP_ERR_BUDGET = -7,            /* request does not fit the server's HBM budget */
@@ -112,7 +113,9 @@ typedef struct {
 
 /* Build options (zero-initialise for defaults). */
 typedef struct {
-  int32_t row_cap;         /* max stored successors per row incl. sink; 0 = 64 */
+  int32_t row_cap;         /* in-domain successors a row keeps in the sliced-ELL columns, <= 255;
+                              0 = 64.  The rest of a longer row goes to its slice's spill
+                              block (HYB); the sink's count is stored apart in either case */
   int32_t no_compact;      /* 1: keep the worst-case entry pool instead of compacting it */
   int32_t threads;         /* CTA size of the FP32 full-window kernel (multiple of 64, <= 512);
                               0 = the autotuner's choice for the workload class (see
@@ -133,9 +136,12 @@ typedef struct mdp_model_t *mdp_model;
  * field extremes as the paper sizes it from the component-wise maximum
  * velocity plus a buffer).  objs_h: host [n_obj], n_obj in [1, 3].
  * On success *out owns all model memory (free with mdp_model_free).
- * Returns MDP_ERR_SUBGRID_OVERFLOW if any landing left the sub-grid and
- * MDP_ERR_ELL_OVERFLOW if a row exceeded row_cap; *out is NULL then.
- * Synchronises `stream` once at the end to read the status word. */
+ * Rows of any length are stored: the first row_cap in-domain successors in
+ * the sliced-ELL columns, the rest in a spill area (allocated only when some
+ * row needs it; the build then runs a second time with the area sized
+ * exactly).  Returns MDP_ERR_SUBGRID_OVERFLOW if any landing left the
+ * sub-grid; *out is NULL then.  Synchronises `stream` once at the end to
+ * read the status word (twice when the first attempt ran out of room). */
 mdp_status mdp_build(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions,
                      int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
                      const mdp_build_opts *opts, void *stream, mdp_model *out);
@@ -150,7 +156,7 @@ typedef struct {
   int32_t precision;
   int64_t rows;            /* A * |S| */
   int64_t nnz;             /* stored successors over all rows (sink entries included) */
-  int32_t max_row_nnz;     /* widest row */
+  int32_t max_row_nnz;     /* widest row in the sliced-ELL columns (<= row_cap) */
   int64_t pool_columns;    /* 32-entry columns of the sliced-ELL entry pool in use */
   int64_t device_bytes;    /* device memory owned by the model */
   int64_t samples;         /* landing evaluations performed (N per sampled (s,a)) */
@@ -159,6 +165,9 @@ typedef struct {
   int32_t launches;        /* kernels the build launched */
   int64_t wide_slices;     /* slices built by the full-window kernel (tables > hist_cap) */
   int64_t nnz_domain;      /* stored successors inside the domain (sink entries excluded) */
+  int64_t spill_rows;      /* rows longer than row_cap (their tails are in the spill area) */
+  int64_t spill_words;     /* 32-bit words of the spill area (33 per spilling slice + entries) */
+  int32_t max_row_len;     /* longest row: in-domain successors, spill included */
 } mdp_model_info_t;
 
 mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *out);

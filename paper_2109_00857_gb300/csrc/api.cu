@@ -205,6 +205,10 @@ static void free_model_memory(mdp_model_t *m, cudaStream_t st) {
   dev_free(m->Vtmp, st);
   dev_free(m->cnt, st);
   dev_free(m->solve_stats_d, st);
+  dev_free(m->spill, st);
+  dev_free(m->spill_off, st);
+  m->spill = nullptr;
+  m->spill_off = nullptr;
   m->pool = nullptr;
   m->slice_off = nullptr;
   m->slice_w = nullptr;
@@ -424,8 +428,12 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
 
   // -- model memory.  The entry pool is sized for an average slice width of
   // kPoolGuess columns first; if the build runs out of columns it is rebuilt
-  // once with the worst case (every slice row_cap wide).
-  const int Wmax = std::min(row_cap, m->nbins + 1);
+  // once with a pool of exactly the columns needed.  A row holds at most
+  // row_cap in-domain successors in the ELL columns (the sink has its own
+  // count); the rest of a longer row goes to a spill area, which the first
+  // attempt does not have: if some row needs it, the rebuild allocates it
+  // with exactly the words counted.
+  const int Wmax = std::min(row_cap, m->nbins);
   const int kPoolGuess = 16;
   // the pool may take at most 60 % of the free device memory; asking the
   // driver costs a round trip, so only pools above 256 MiB ask
@@ -462,6 +470,20 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.slice_w = m->slice_w; ba.nnz = m->nnz; ba.sinkc = m->sinkc;
   ba.R = m->R; ba.cnt = m->cnt;
   ba.slice_begin = 0; ba.slice_end = m->n_slices;
+  // spill area: the caller's size when it fixes the pool (the server), else none yet
+  uint64_t spill_cap = (lim && lim->pool_cols) ? lim->spill_words : 0;
+  auto alloc_spill = [&](uint64_t words) -> cudaError_t {
+    dev_free(m->spill, st);
+    m->spill = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!m->spill_off) e = dev_alloc((void **)&m->spill_off, sizeof(uint32_t) * (size_t)m->n_slices, st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&m->spill, sizeof(uint32_t) * (size_t)std::max<uint64_t>(words, 1), st);
+    ba.spill = m->spill;
+    ba.spill_off = m->spill_off;
+    ba.spill_cap_words = words;
+    return e;
+  };
+  if (spill_cap) TRY(alloc_spill(spill_cap));
   // launch shapes: the caller's, else the autotuner's for this workload class, else defaults
   Tuning tun;
   tuning_lookup(tuning_key(m->A_pad, env->K, N, Nc, n_obj, prec), &tun);
@@ -511,17 +533,22 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
     cudaEventRecord(ev1, st);
     TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    if (c[CNT_POOL_FULL] == 0 || attempt > 0) break;
-    // The pool ran out.  The column counter holds every slice's width even
-    // for the slices that did not fit, i.e. exactly the columns the build
-    // needs: rebuild once with a pool of that size (counters reset, sampled
-    // Y kept) -- unless the caller fixed the pool size, then report the need.
-    const uint64_t need = c[CNT_POOL_COLS];
+    const bool pool_full = c[CNT_POOL_FULL] != 0, spill_full = c[CNT_SPILL_FULL] != 0;
+    if ((!pool_full && !spill_full) || attempt > 0) break;
+    // The pool or the spill area ran out.  The column counter holds every
+    // slice's width even for the slices that did not fit, and the spill
+    // counter every spill block's words, i.e. exactly what the build needs:
+    // rebuild once with those sizes (counters reset, sampled Y kept) --
+    // unless the caller fixed the sizes, then report the need.
+    const uint64_t need = pool_full ? c[CNT_POOL_COLS] : cap_cols;
+    const uint64_t sneed = spill_full ? c[CNT_SPILL_WORDS] : spill_cap;
     if (lim && lim->pool_cols) {
       lim->pool_cols_needed = need;
-      char buf[160];
-      snprintf(buf, sizeof buf, "the entry pool needs %llu columns, above the %llu allowed",
-               (unsigned long long)need, (unsigned long long)lim->pool_cols);
+      lim->spill_words_needed = sneed;
+      char buf[200];
+      snprintf(buf, sizeof buf, "the model needs %llu pool columns and %llu spill words, above the %llu and %llu allowed",
+               (unsigned long long)need, (unsigned long long)sneed, (unsigned long long)lim->pool_cols,
+               (unsigned long long)spill_cap);
       set_error(buf);
       if (Yown) dev_free(Yown, st);
       if (sig_d) dev_free(sig_d, st);
@@ -531,14 +558,21 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
       cudaEventDestroy(evk);
       return fail(MDP_ERR_BUDGET);
     }
-    if (need > budget_cols) break;   // does not fit the device: reported as MDP_ERR_OOM below
-    dev_free(m->pool, st);
-    cap_cols = std::max<uint64_t>(need, 1);
-    TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+    // does not fit the device (or the 32-bit block offsets): reported as MDP_ERR_OOM below
+    if (need > budget_cols || sneed > budget_cols * 32 || sneed >= (uint64_t)kNoSlice) break;
+    if (pool_full) {
+      dev_free(m->pool, st);
+      cap_cols = std::max<uint64_t>(need, 1);
+      TRY(dev_alloc((void **)&m->pool, (size_t)cap_cols * 128, st));
+      ba.pool = m->pool;
+      ba.pool_cap_cols = cap_cols;
+    }
+    if (spill_full) {
+      spill_cap = sneed;
+      TRY(alloc_spill(spill_cap));
+    }
     TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_CAPPED, st));
     TRY(cudaMemsetAsync(m->cnt + CNT_WORK, 0, sizeof(unsigned long long) * (CNT_N - CNT_WORK), st));
-    ba.pool = m->pool;
-    ba.pool_cap_cols = cap_cols;
   }
   if (Yown) dev_free(Yown, st);
   if (sig_d) dev_free(sig_d, st);
@@ -560,21 +594,26 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
     set_error(buf);
     return fail(MDP_ERR_SUBGRID_OVERFLOW);
   }
-  if (c[CNT_ROW_CAP]) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "%llu row(s) had more than %d successors (raise row_cap)", c[CNT_ROW_CAP], Wmax);
-    set_error(buf);
-    return fail(MDP_ERR_ELL_OVERFLOW);
-  }
-  if (c[CNT_POOL_FULL]) {
-    set_error("entry pool capacity exhausted (device memory budget)");
+  if (c[CNT_POOL_FULL] || c[CNT_SPILL_FULL]) {
+    set_error(c[CNT_POOL_FULL] ? "entry pool capacity exhausted (device memory budget)"
+                               : "spill area exhausted (device memory budget)");
     return fail(MDP_ERR_OOM);
   }
   m->pool_cols = c[CNT_POOL_COLS];
   m->nnz_total = (int64_t)c[CNT_NNZ];
   m->nnz_domain = (int64_t)c[CNT_DOMAIN];
   m->max_row_nnz = (int32_t)c[CNT_MAXROW];
+  m->max_row_len = c[CNT_MAXLEN] ? (int32_t)c[CNT_MAXLEN] : m->max_row_nnz;
   m->samples = (int64_t)c[CNT_SAMPLES];
+  m->spill_rows = (int64_t)c[CNT_SPILL_ROWS];
+  m->spill_words = c[CNT_SPILL_WORDS];
+  if (m->spill_words == 0) {   // no row beyond row_cap: no spill area
+    dev_free(m->spill, st);
+    dev_free(m->spill_off, st);
+    m->spill = nullptr;
+    m->spill_off = nullptr;
+    spill_cap = 0;
+  }
   // -- compaction: the columns in use move into a pool of exactly that size,
   // in slice order (a run of consecutive slices is then one contiguous copy
   // for the solver)
@@ -588,7 +627,7 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
     cap_cols = std::max<uint64_t>(m->pool_cols, 1);
   }
   m->device_bytes = (int64_t)cap_cols * 128 + 5 * m->n_slices + 3 * m->rows_pad + (int64_t)fsz * m->rows_pad * n_obj +
-                    nS + 4 * m->nbins + 8 * CNT_N;
+                    nS + 4 * m->nbins + 8 * CNT_N + (m->spill ? 4 * (int64_t)(m->n_slices + spill_cap) : 0);
   *out = m;
 #undef TRY
   return MDP_OK;
@@ -623,6 +662,9 @@ extern "C" mdp_status mdp_model_info(mdp_model m, mdp_model_info_t *o) {
   o->launches = m->launches;
   o->wide_slices = m->deferred;
   o->nnz_domain = m->nnz_domain;
+  o->spill_rows = m->spill_rows;
+  o->spill_words = (int64_t)m->spill_words;
+  o->max_row_len = m->max_row_len;
   return MDP_OK;
 }
 
@@ -707,6 +749,8 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   SolveArgs a;
   a.pool = m->pool; a.slice_off = m->slice_off; a.slice_w = m->slice_w; a.nnz = m->nnz;
   a.wcap = std::max(1, m->max_row_nnz);
+  a.spill = m->spill;
+  a.spill_off = m->spill_off;
   a.R = io.R[0];
   a.cls = m->cls; a.delta = m->delta;
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;

@@ -226,6 +226,12 @@ extern "C" mdp_status mdp_batch_create(const mdp_batch_item *items_h, int32_t n,
       set_error("batch item " + std::to_string(i) + ": " + mdp_last_error());
       return fail(s);
     }
+    if (cm->spill_words) {   // the batched build and sweeps keep rows in the ELL columns only
+      free_model_on_stream(cm, b->st);
+      set_error("batch item " + std::to_string(i) + ": a row has more than the row cap's successors "
+                "(batched models keep no spill area; build it with mdp_build)");
+      return fail(MDP_ERR_ELL_OVERFLOW);
+    }
     it.L = cm->L;
     it.pool_cols = (int64_t)cm->pool_cols;
     it.width = std::max(1, cm->max_row_nnz);
@@ -407,7 +413,7 @@ extern "C" mdp_status mdp_batch_run(mdp_batch b, void *stream, int32_t *sweeps_h
       set_error(which + "a landing left the neighbouring sub-grid");
       return MDP_ERR_SUBGRID_OVERFLOW;
     }
-    if (c[CNT_ROW_CAP]) {
+    if (c[CNT_ROW_CAP] || c[CNT_SPILL_FULL]) {
       set_error(which + "a row exceeded the row cap");
       return MDP_ERR_ELL_OVERFLOW;
     }

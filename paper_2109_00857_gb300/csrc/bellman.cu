@@ -174,7 +174,7 @@ struct PipeRange {
   int64_t s_lo, s_hi;     // states whose V this launch writes
   int stage_bytes;        // bytes per stage
   int dtab_smem;          // 1: delta table staged in shared memory
-  int grouped;            // 1: bellman_kernel_g (kGS states per warp step); 2: bellman_kernel_ws
+  int grouped;            // 1: bellman_body_g (kGS states per warp step, batched sweeps); 2: bellman_kernel_ws
                           // (stage_bytes = entry bytes per slot)
 };
 
@@ -216,6 +216,25 @@ struct VSet {
   int16_t *pol[NO];
   unsigned long long *res[NO];
 };
+
+// The tail of row `lane` of slice sl that the build put in the slice's spill
+// block (HYB), added to the row's sums in its stored (ascending) order after
+// the ELL columns: the same sum as over one plain row.  Called only for
+// models with a spill area (a.spill_off != nullptr).
+template <typename RT, int NO>
+__device__ __forceinline__ void add_spill(const SolveArgs &a, int64_t sl, int lane, const VPack<RT, NO> *Vn,
+                                          Acc<RT> (&acc)[NO]) {
+  const uint32_t off = __ldg(a.spill_off + sl);
+  if (off == kNoSlice) return;
+  const uint32_t *blk = a.spill + off;
+  const uint32_t b = __ldg(blk + lane), e = __ldg(blk + lane + 1);
+  for (uint32_t i = b; i < e; ++i) {
+    const uint32_t w = __ldg(blk + kSpillHdr + i);
+    const VPack<RT, NO> g = Vn[(int)(int16_t)(w & 0xFFFFu)];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, g.v[o], a.N);
+  }
+}
 
 template <typename RT, int NO>
 __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
@@ -332,6 +351,7 @@ __device__ __forceinline__ void bellman_body(const SolveArgs &a, const VSet<RT, 
 #pragma unroll
       for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, g.v[o], a.N);
     }
+    if (a.spill_off) add_spill<RT, NO>(a, sl0 + (int64_t)j * kWarps, lane, Vn, acc);
     __syncwarp();
     if (j + kDepth < n_mine) issue(j + kDepth, st);   // refill the stage just read
     if (++st == kDepth) {
@@ -712,22 +732,6 @@ __device__ __forceinline__ void bellman_body_g(const SolveArgs &a, const VSet<RT
   }
 }
 
-template <typename RT, int NO>
-__global__ void __launch_bounds__(32 * kWarpsG, 1) bellman_kernel_g(SolveArgs a, VSet<RT, NO> v,
-                                                                                       int k, PipeRange pr) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ double wmax[kWarpsG * NO];
-  __shared__ int wst_s[kWarpsG * kDepth * kGS];   // columns of each slot of each stage
-  if (a.lflags && k >= 1 && !active_range(a, k, pr, blockIdx.x == 0)) return;
-  // CTA ranges in whole groups so that a group never straddles two CTAs
-  const int64_t total = pr.sl_hi - pr.sl_lo;
-  const int64_t groups = (total + kGS - 1) / kGS;
-  const int64_t per_cta = (groups + gridDim.x - 1) / gridDim.x * kGS;
-  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
-  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
-  bellman_body_g<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, wst_s);
-}
-
 // ---- warp-specialized sweep: a producer warp stages rounds of slices ----
 // Models with one state per slice (A_pad = 32).  Each CTA has kWsCons
 // consumer warps and one producer warp, and walks its block of consecutive
@@ -969,6 +973,7 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
         ph ^= 1u;
       }
       if (!mine) continue;
+      if (a.spill_off) add_spill<RT, NO>(a, s, lane, v.in + ((s + Nc <= nS) ? s + Nc : nS), acc);
       RT qv[NO];
       int qa[NO];
 #pragma unroll
@@ -1322,26 +1327,7 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
     *blocks = (int)b;
     return cudaSuccess;
   }
-  // grouped sweep for one state per slice while kWarpsG warps x kDepth
-  // stages of kGS slots fit one CTA's shared memory (slices up to 13
-  // columns); wider models take the warp-per-slice kernel
-  pr->grouped = (a.spw == 1 && grouped_smem(a.wcap) <= kGroupedSmemMax) ? 1 : 0;
-  if (pr->grouped) {
-    pr->stage_bytes = kGS * slot_bytes_g(a.wcap);
-    *smem = grouped_smem(a.wcap);
-    cudaError_t e = allow_max_smem((const void *)bellman_kernel_g<RT, NO>);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel_g<RT, NO>, 32 * kWarpsG, *smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t b = (int64_t)num_sms() * per_sm;
-    const int64_t want = (slices + 2 * kGS * kWarpsG - 1) / (2 * kGS * kWarpsG);   // >= 2 groups per warp
-    if (b > want) b = want;
-    if (b < 1) b = 1;
-    *blocks = (int)b;
-    return cudaSuccess;
-  }
+  pr->grouped = 0;   // several states per slice: the warp-per-slice kernel
   pr->stage_bytes = stage_bytes_for(a.wcap);
   *smem = 256 + (size_t)kWarps * kDepth * pr->stage_bytes;
   if (*smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -1404,8 +1390,6 @@ static void launch_sweep(const SolveArgs &a, const VSet<RT, NO> &v, int k, const
                          size_t smem, cudaStream_t st) {
   if (pr.grouped == 2)
     bellman_kernel_ws<RT, NO><<<blocks, 32 * (kWsCons + 1), smem, st>>>(a, v, k, pr);
-  else if (pr.grouped)
-    bellman_kernel_g<RT, NO><<<blocks, 32 * kWarpsG, smem, st>>>(a, v, k, pr);
   else
     bellman_kernel<RT, NO><<<blocks, 32 * kWarps, smem, st>>>(a, v, k, pr);
 }
@@ -1553,13 +1537,21 @@ cudaError_t launch_layered_multi(const SolveArgs &a, int precision, int nt, cons
 
 // -------------------------------------------------------------- export ----
 // Paper layout row r = a*|S| + s.
+// entries of internal row ir = 32 sl + lane held in its slice's spill block
+__device__ __forceinline__ int spill_len(const uint32_t *spill, const uint32_t *spill_off, int64_t sl, int lane) {
+  if (!spill_off) return 0;
+  const uint32_t off = spill_off[sl];
+  return off == kNoSlice ? 0 : (int)(spill[off + lane + 1] - spill[off + lane]);
+}
+
 __global__ void export_count_kernel(const uint8_t *__restrict__ nnz, const uint16_t *__restrict__ sinkc,
+                                    const uint32_t *__restrict__ spill, const uint32_t *__restrict__ spill_off,
                                     int64_t nS, int A, int A_pad, int64_t *__restrict__ rowlen) {
   const int64_t rows = nS * A;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t act = r / nS, s = r % nS;
     const int64_t ir = s * A_pad + act;
-    rowlen[r] = nnz[ir] + (sinkc[ir] ? 1 : 0);
+    rowlen[r] = nnz[ir] + spill_len(spill, spill_off, ir / 32, (int)(ir % 32)) + (sinkc[ir] ? 1 : 0);
   }
 }
 
@@ -1657,6 +1649,7 @@ cudaError_t launch_pool_reorder(const uint32_t *pool, uint32_t *out, uint32_t *s
 template <typename RT>
 __global__ void export_fill_kernel(const uint32_t *__restrict__ pool, const uint32_t *__restrict__ slice_off,
                                    const uint8_t *__restrict__ nnz, const uint16_t *__restrict__ sinkc,
+                                   const uint32_t *__restrict__ spill, const uint32_t *__restrict__ spill_off,
                                    const RT *__restrict__ Rsrc, int64_t nS, int64_t Nc, int A, int A_pad,
                                    int spw, int64_t n_slices, const int64_t *__restrict__ rowptr,
                                    int64_t *col, int32_t *count, RT *Rdst) {
@@ -1670,7 +1663,7 @@ __global__ void export_fill_kernel(const uint32_t *__restrict__ pool, const uint
     const int64_t r = (int64_t)act * nS + s;
     if (Rdst) Rdst[r] = Rsrc[ir];
     if (!col && !count) continue;
-    const int e = nnz[ir];
+    int e = nnz[ir];
     const int64_t o = rowptr[r];
     if (e > 0) {
       const uint32_t off = slice_off[sl];
@@ -1679,6 +1672,16 @@ __global__ void export_fill_kernel(const uint32_t *__restrict__ pool, const uint
         if (col) col[o + k] = s + Nc + (int64_t)(int16_t)(w & 0xFFFFu);
         if (count) count[o + k] = (int32_t)(w >> 16);
       }
+    }
+    const int ns = spill_len(spill, spill_off, sl, lane);
+    if (ns > 0) {   // the row's tail, after its ELL entries (ascending order continues)
+      const uint32_t *ent = spill + spill_off[sl] + kSpillHdr + spill[spill_off[sl] + lane];
+      for (int k = 0; k < ns; ++k) {
+        const uint32_t w = ent[k];
+        if (col) col[o + e + k] = s + Nc + (int64_t)(int16_t)(w & 0xFFFFu);
+        if (count) count[o + e + k] = (int32_t)(w >> 16);
+      }
+      e += ns;
     }
     if (sinkc[ir]) {
       if (col) col[o + e] = nS;
@@ -1693,7 +1696,8 @@ cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_
   int64_t blocks = (rows + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  export_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(m->nnz, m->sinkc, m->nS, m->A, m->A_pad, rowptr);
+  export_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(m->nnz, m->sinkc, m->spill, m->spill_off, m->nS, m->A,
+                                                         m->A_pad, rowptr);
   cudaError_t e = cudaMemsetAsync(rowptr + rows, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return e;
   // scan scratch: geometric series of tile counts
@@ -1710,11 +1714,13 @@ cudaError_t launch_export(const mdp_model_t *m, int obj, int64_t *rowptr, int64_
   const size_t esz = (m->precision == MDP_FP64_CHECK) ? 8 : 4;
   if (m->precision == MDP_FP64_CHECK)
     export_fill_kernel<double><<<(unsigned)fb, 256, 0, st>>>(
-        m->pool, m->slice_off, m->nnz, m->sinkc, static_cast<const double *>(m->R) + (size_t)obj * m->rows_pad,
+        m->pool, m->slice_off, m->nnz, m->sinkc, m->spill, m->spill_off,
+        static_cast<const double *>(m->R) + (size_t)obj * m->rows_pad,
         m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (double *)R);
   else
     export_fill_kernel<float><<<(unsigned)fb, 256, 0, st>>>(
-        m->pool, m->slice_off, m->nnz, m->sinkc, static_cast<const float *>(m->R) + (size_t)obj * m->rows_pad,
+        m->pool, m->slice_off, m->nnz, m->sinkc, m->spill, m->spill_off,
+        static_cast<const float *>(m->R) + (size_t)obj * m->rows_pad,
         m->nS, m->Nc, m->A, m->A_pad, m->spw, m->n_slices, rowptr, col, count, (float *)R);
   (void)esz;
   e = cudaGetLastError();

@@ -87,15 +87,60 @@ __device__ __forceinline__ uint32_t entry_word(int off, uint32_t n) {
   return ((uint32_t)off & 0xFFFFu) | (n << 16);
 }
 
+// HYB spill of slice sl (the whole warp calls it): sp = this lane's in-domain
+// successors beyond row_cap.  When any lane has some, allocates the slice's
+// spill block (kSpillHdr header words + the entries) from the model's spill
+// area, writes the header and spill_off[sl], and returns the word index of this
+// lane's first spill entry; returns -1 when nothing is to be stored (no spill,
+// or no room: the need is counted in CNT_SPILL_WORDS either way, and a slice
+// without room in CNT_SPILL_FULL, so that the build can be rerun with an area
+// of exactly the size needed).
+__device__ __forceinline__ int64_t spill_alloc(const BuildArgs &a, int64_t sl, int sp) {
+  const int lane = threadIdx.x & 31;
+  int incl = sp;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += x;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) {
+    if (lane == 0 && a.spill_off) a.spill_off[sl] = kNoSlice;
+    return -1;
+  }
+  const unsigned rows = __popc(__ballot_sync(0xffffffffu, sp > 0));
+  unsigned long long base = 0;
+  if (lane == 0) {
+    base = atomicAdd(&a.cnt[CNT_SPILL_WORDS], (unsigned long long)(total + kSpillHdr));
+    atomicAdd(&a.cnt[CNT_SPILL_ROWS], (unsigned long long)rows);
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const bool fits = a.spill && base + (unsigned long long)(total + kSpillHdr) <= a.spill_cap_words;
+  if (lane == 0) {
+    if (!fits) atomicAdd(&a.cnt[CNT_SPILL_FULL], 1ULL);
+    if (a.spill_off) a.spill_off[sl] = fits ? (uint32_t)base : kNoSlice;
+  }
+  if (!fits) return -1;
+  uint32_t *blk = a.spill + base;
+  blk[lane] = (uint32_t)(incl - sp);
+  if (lane == 31) blk[32] = (uint32_t)total;
+  return (int64_t)base + kSpillHdr + (incl - sp);
+}
+
 // Executed by one full warp for one slice.  Lane l owns internal row
 // ir = sl*32 + l.  Scans its histogram column hist[b*32 + l] over the bins of
 // [lo_x, hi_x] x [lo_y, hi_y] (sub-grid offsets) in ascending bin order,
 // zeroes what it reads, classifies each landing cell (outside the domain or an
-// obstacle at t+1 -> sink), stages entry words in stage[k*32 + l],
+// obstacle at t+1 -> sink), stages the k-th entry word in its own column at
+// hist[k*32 + l] (bin k <= the bin just read, so already read and zeroed: the
+// histogram is the stage, and the kernels need no shared memory for it),
 // accumulates R = sum_b (count_b/N) r_b + (count_sink/N) r_outbound in that
-// order, then allocates the slice's columns from the pool and writes them.
+// order, then allocates the slice's columns from the pool, writes them and
+// zeroes the staged words again.
+// Entries beyond row_cap go to the slice's spill block (HYB); a box of at
+// most row_cap bins cannot have any, otherwise a first pass counts them.
 template <typename RT>
-__device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, int64_t sl,
+__device__ void emit_slice(const BuildArgs &a, uint32_t *hist, int64_t sl,
                            int kind, bool row_ok, int lo_x, int hi_x, int lo_y, int hi_y) {
   const int lane = threadIdx.x & 31;
   const int q = lane / a.A_pad, act = lane % a.A_pad;
@@ -104,12 +149,29 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
   int e = 0;              // in-domain entries
   uint32_t sink = 0;      // realizations ending in the sink
   RT Racc[3] = {RT(0), RT(0), RT(0)};
-  bool cap_hit = false;
 
   lo_x = max(lo_x, -a.h);
   lo_y = max(lo_y, -a.h);
   hi_x = min(hi_x, a.h);
   hi_y = min(hi_y, a.h);
+  int spill_n = 0;   // this row's in-domain successors beyond row_cap
+  if ((hi_x - lo_x + 1) * (hi_y - lo_y + 1) > a.row_cap && kind == KIND_SAMPLE && row_ok) {
+    const int64_t t = s / a.Nc, c = s % a.Nc;
+    const int i = (int)(c % a.nx), j = (int)(c / a.nx);
+    const int64_t nxt = (t + 1) * a.Nc;
+    int cnt = 0;
+    for (int dj = lo_y; dj <= hi_y; ++dj) {
+      const int jp = j + dj;
+      for (int di = lo_x; di <= hi_x; ++di) {
+        if (hist[(size_t)((dj + a.h) * a.L + a.h + di) * 32 + lane] == 0) continue;
+        const int ip = i + di;
+        const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
+        if (inside && !(a.cls[nxt + (int64_t)jp * a.nx + ip] & CLS_OBSTACLE)) ++cnt;
+      }
+    }
+    spill_n = max(cnt - a.row_cap, 0);
+  }
+  const int64_t sp_at = spill_alloc(a, sl, spill_n);
   if (kind == KIND_SINK) {
     sink = (uint32_t)a.N;
     for (int o = 0; o < a.rw.n_obj; ++o) {
@@ -143,11 +205,9 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
           sink += n;
           continue;
         }
-        if (e >= a.row_cap) {
-          cap_hit = true;
-          continue;
-        }
-        stage[e * 32 + lane] = entry_word(dj * a.nx + di, n);
+        const uint32_t wd = entry_word(dj * a.nx + di, n);
+        if (e < a.row_cap) hist[e * 32 + lane] = wd;
+        else if (sp_at >= 0) a.spill[sp_at + (e - a.row_cap)] = wd;
         ++e;
         const bool is_t = (ccls & CLS_TARGET) != 0;
         RT g_sp = RT(0);
@@ -178,14 +238,11 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
       sink = 0;
     }
   }
-  if (e + (sink > 0 ? 1 : 0) > a.row_cap) cap_hit = true;
-  if (cap_hit) {
-    atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
-    e = 0;
-  }
+  int ell = min(e, a.row_cap);   // entries in the ELL columns
+  const int staged = ell;        // histogram words holding them
 
   // slice width = widest row; allocate columns from the pool (bump allocator)
-  int W = e;
+  int W = ell;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) W = max(W, __shfl_xor_sync(0xffffffffu, W, off));
   unsigned long long base = 0;
@@ -195,16 +252,19 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, uint32_t *stage, 
   if (!fits) {
     if (lane == 0) atomicAdd(&a.cnt[CNT_POOL_FULL], 1ULL);
     e = 0;
+    ell = 0;
   }
   if (fits && W > 0) {
     uint32_t *dst = a.pool + base * 32 + lane;
-    for (int k = 0; k < W; ++k) dst[(size_t)k * 32] = (k < e) ? stage[k * 32 + lane] : 0u;
+    for (int k = 0; k < W; ++k) dst[(size_t)k * 32] = (k < ell) ? hist[k * 32 + lane] : 0u;
   }
+  for (int k = 0; k < staged; ++k) hist[k * 32 + lane] = 0u;   // the histogram is zero again
+  if (e > ell) atomicMax(&a.cnt[CNT_MAXLEN], (unsigned long long)e);
   if (lane == 0) {
     a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
     a.slice_w[sl] = (fits && W > 0) ? (uint8_t)W : (uint8_t)0;
   }
-  a.nnz[ir] = (uint8_t)e;
+  a.nnz[ir] = (uint8_t)ell;
   a.sinkc[ir] = (uint16_t)sink;
   int tot = e + (sink > 0 ? 1 : 0), dom = e;
 #pragma unroll

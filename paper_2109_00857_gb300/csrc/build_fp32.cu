@@ -58,8 +58,7 @@ __device__ __forceinline__ void load_y(const float *__restrict__ yw, float (&y)[
 template <int KT>
 __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long long &s_slice) {
   uint32_t *hist = smem;                                             // [nbins][32]
-  uint32_t *stage = hist + (size_t)a.nbins * 32;                     // [row_cap][32]
-  float2 *ubuf = reinterpret_cast<float2 *>(stage + (size_t)a.row_cap * 32);  // [chunk][spw]
+  float2 *ubuf = reinterpret_cast<float2 *>(hist + (size_t)a.nbins * 32);    // [chunk][spw]
   float *red = reinterpret_cast<float *>(ubuf + (size_t)a.chunk * a.spw);    // [nwarps][spw][4]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -205,7 +204,7 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
         if (!row_ok) atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
         else atomicAdd(&a.cnt[CNT_SAMPLES], (unsigned long long)a.N);
       }
-      emit_slice<float>(a, hist, stage, sl, kind_l, row_ok, lox, hix, loy, hiy);
+      emit_slice<float>(a, hist, sl, kind_l, row_ok, lox, hix, loy, hiy);
     }
     __syncthreads();
   }
@@ -245,7 +244,7 @@ cudaError_t launch_build_fp32_batch(const BuildArgs *items_d, int n, size_t smem
 }
 
 size_t fp32_smem_bytes(const BuildArgs &a, int threads) {
-  return (size_t)a.nbins * 32 * 4 + (size_t)a.row_cap * 32 * 4 + (size_t)a.chunk * a.spw * 8 +
+  return (size_t)a.nbins * 32 * 4 + (size_t)a.chunk * a.spw * 8 +
          (size_t)(threads / 32) * a.spw * 16;
 }
 

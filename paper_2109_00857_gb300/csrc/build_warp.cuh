@@ -395,12 +395,11 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   } else if (kind_l == KIND_SINK) {
     sink = (uint32_t)N;
   }
-  const bool cap_hit = e + (sink > 0 ? 1 : 0) > a.row_cap;
-  if (cap_hit) {
-    atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
-    e = 0;
-  }
-  int W = e;
+  // the first row_cap in-domain successors go to the ELL columns, the rest to
+  // the slice's spill block (HYB)
+  int ell = min(e, a.row_cap);
+  const int64_t sp_at = spill_alloc(a, sl, e - ell);
+  int W = ell;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) W = max(W, __shfl_xor_sync(0xffffffffu, W, off));
   unsigned long long base = 0;
@@ -410,7 +409,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   if (!fits && lane == 0) atomicAdd(&a.cnt[CNT_POOL_FULL], 1ULL);
   float Racc[3] = {0.f, 0.f, 0.f};
   uint32_t *dst = a.pool + base * 32 + lane;
-  const bool write = fits && !cap_hit;
+  const bool write = fits;
   int k = 0;
   if (kind_l == KIND_SAMPLE && active) {
     const float F = a.act.F[a_l];
@@ -424,7 +423,12 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
         const bool inside = ip >= 0 && ip < nx && jp >= 0 && jp < ny;
         const uint8_t cc = inside ? cls[nxt + (int64_t)jp * nx + ip] : CLS_OBSTACLE;
         if (cc & CLS_OBSTACLE) continue;
-        if (write) dst[(size_t)k * 32] = entry_word(dj * nx + di, n);
+        const uint32_t wd = entry_word(dj * nx + di, n);
+        if (k < ell) {
+          if (write) dst[(size_t)k * 32] = wd;
+        } else if (sp_at >= 0) {
+          a.spill[sp_at + (k - ell)] = wd;
+        }
         ++k;
         const bool is_t = (cc & CLS_TARGET) != 0;
         const float g_sp = gbar ? gbar[nxt + (int64_t)jp * nx + ip] : 0.f;
@@ -440,16 +444,17 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   }
   if (!write) {
     e = 0;
-    k = 0;
+    ell = 0;
   }
   if (write)   // zero padding up to the slice width
-    for (int kk = k; kk < W; ++kk) dst[(size_t)kk * 32] = 0u;
+    for (int kk = ell; kk < W; ++kk) dst[(size_t)kk * 32] = 0u;
+  if (e > ell) atomicMax(&a.cnt[CNT_MAXLEN], (unsigned long long)e);
   if (!fits) sink = 0;
   if (lane == 0) {
     a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
     a.slice_w[sl] = (fits && W > 0) ? (uint8_t)W : (uint8_t)0;
   }
-  a.nnz[ir] = (uint8_t)e;
+  a.nnz[ir] = (uint8_t)ell;
   a.sinkc[ir] = (uint16_t)sink;
   for (int o = 0; o < a.rw.n_obj; ++o) static_cast<float *>(a.R)[(int64_t)o * a.rows_pad + ir] = Racc[o];
   int dom = e;

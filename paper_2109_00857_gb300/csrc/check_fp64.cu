@@ -127,7 +127,6 @@ cudaError_t launch_sample_coeffs(int nt, int N, int K, const double *sigma_d, ui
 __global__ void build_fp64_kernel(BuildArgs a) {
   extern __shared__ uint32_t smem[];
   uint32_t *hist = smem;                                   // [nbins][32]
-  uint32_t *stage = hist + (size_t)a.nbins * 32;           // [row_cap][32]
   __shared__ long long s_slice;
   const int tid = threadIdx.x;
   for (int i = tid; i < a.nbins * 32; i += blockDim.x) hist[i] = 0;
@@ -184,14 +183,14 @@ __global__ void build_fp64_kernel(BuildArgs a) {
       const int q = tid / a.A_pad, act = tid % a.A_pad;
       int kind = state_kind(a, sl * a.spw + q);
       if (act >= a.A) kind = KIND_NONE;
-      emit_slice<double>(a, hist, stage, sl, kind, true, -a.h, a.h, -a.h, a.h);
+      emit_slice<double>(a, hist, sl, kind, true, -a.h, a.h, -a.h, a.h);
     }
     __syncthreads();
   }
 }
 
 cudaError_t launch_build_fp64(const BuildArgs &a, cudaStream_t st) {
-  const size_t smem = (size_t)a.nbins * 32 * 4 + (size_t)a.row_cap * 32 * 4;
+  const size_t smem = (size_t)a.nbins * 32 * 4;
   cudaError_t e = allow_max_smem((const void *)build_fp64_kernel);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

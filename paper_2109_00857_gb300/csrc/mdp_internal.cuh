@@ -47,8 +47,22 @@ enum {
   CNT_DEFER_N = 9,       // slices the warp kernel handed to the CTA kernel
   CNT_DEFER_WORK = 10,   // work-queue head of the CTA kernel over the deferred list
   CNT_DOMAIN = 11,       // stored in-domain successors (sink entries excluded)
+  CNT_SPILL_WORDS = 12,  // spill words requested (headers included), stored or not
+  CNT_SPILL_FULL = 13,   // slices whose spill block did not fit the spill area
+  CNT_SPILL_ROWS = 14,   // rows with entries beyond row_cap
+  CNT_MAXLEN = 15,       // longest row (in-domain successors + sink), spill included
   CNT_N = 16
 };
+
+// HYB spill.  A row keeps its first row_cap in-domain successors in the
+// slice's ELL columns; the rest of the row (still in ascending order) goes to
+// its slice's spill block at spill[spill_off[slice]]: kSpillHdr words
+// start[0..32] (start[l] = first entry of row l of the slice relative to the
+// block's entries, start[32] = the block's entry count), then the entry words
+// (the ELL's 16-bit offset | 16-bit count).  Summing a row's ELL columns and
+// then its spill entries is the same ascending-order sum as over one plain
+// row.  Slices without a spill block hold kNoSlice in spill_off.
+constexpr int kSpillHdr = 33;
 
 constexpr int kRankBuckets = 128;
 
@@ -106,6 +120,11 @@ struct BuildArgs {
   int32_t cap_bins;          // fine-table words per warp of the warp kernel
   uint32_t *defer;           // slices deferred by the warp kernel ([n_slices])
   const uint32_t *defer_in;  // non-NULL: the CTA kernel works on this list (count CNT_DEFER_N)
+  // HYB spill area (nullptr: none; rows beyond row_cap then only count their
+  // need in CNT_SPILL_WORDS / CNT_SPILL_FULL)
+  uint32_t *spill;
+  uint32_t *spill_off;       // [n_slices] word offset of the slice's block, or kNoSlice
+  uint64_t spill_cap_words;
 };
 
 struct mdp_model_impl;
@@ -144,6 +163,13 @@ struct mdp_model_t {
   int32_t pool_ordered;       // 1: the pool holds the slices in slice order, back to back
                               // (slice_off[sl + 1] = slice_off[sl] + slice_w[sl])
   int32_t sweep_smem_kb;      // shared memory of the one-state-per-slice Bellman sweep (0: default)
+  // HYB spill (nullptr when no row is longer than row_cap)
+  uint32_t *spill;            // [spill_words] per-slice blocks (kSpillHdr words + entries)
+  uint32_t *spill_off;        // [n_slices] block offset or kNoSlice
+  uint64_t spill_words;
+  int64_t spill_rows;         // rows with entries beyond row_cap
+  int64_t spill_entries;      // entries held in the spill blocks
+  int32_t max_row_len;        // longest row (in-domain successors + sink)
 };
 
 namespace mdpgb {
@@ -211,6 +237,8 @@ struct SolveArgs {
   int32_t sweep_smem_kb = 0;  // shared memory of the one-state-per-slice sweep (0: its default)
   long long wait_cycles = 0;  // bounded waits give up after this many clock cycles (0: ~2 s)
   uint32_t test_extra_tx = 0; // failure injection (tests): bytes one wait expects that never arrive
+  const uint32_t *spill = nullptr;      // HYB spill blocks (nullptr: the model has none)
+  const uint32_t *spill_off = nullptr;  // [n_slices]
 };
 // Launch shapes chosen by the autotuner (mdp_autotune) per workload class;
 // every choice gives the same model and values bit for bit.
@@ -316,6 +344,8 @@ struct BuildHook {
 struct BuildLimits {
   uint64_t pool_cols = 0;          // in: pool columns to allocate (0: the build's own guess)
   uint64_t pool_cols_needed = 0;   // out (MDP_ERR_BUDGET): the columns the slices need
+  uint64_t spill_words = 0;        // in (with pool_cols): spill words to allocate (0: none)
+  uint64_t spill_words_needed = 0; // out (MDP_ERR_BUDGET): the spill words the rows need
 };
 mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
                       int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,

@@ -120,6 +120,8 @@ extern "C" mdp_status mdp_solve_noalloc(mdp_model m, int32_t obj, double tol, in
   a.err = reinterpret_cast<int *>(sd + 2);
   a.nt = m->nt;
   a.pool_ordered = m->pool_ordered;
+  a.spill = m->spill;
+  a.spill_off = m->spill_off;
   if ((size_t)m->nt + 1 <= kNoAllocLayers) {
     a.work = reinterpret_cast<unsigned long long *>(scratch + kNoAllocVBytes + kNoAllocStatus);
     a.lflags = scratch + kNoAllocVBytes + kNoAllocStatus + kNoAllocWork;

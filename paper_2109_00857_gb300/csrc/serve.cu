@@ -73,6 +73,7 @@ struct Job {
   int64_t bytes = 0;             // device memory charged now
   int64_t peak_bytes = 0;        // the largest charge it held (reported)
   uint64_t pool_cols = 0;        // entry-pool size the charge covers
+  uint64_t spill_words = 0;      // spill-area size the charge covers (rows beyond the row cap)
   int level = 0;                 // stream priority level (0 = highest)
   mdp_status status = MDP_ERR_PENDING;
   std::string error;
@@ -129,8 +130,9 @@ ReqShape req_shape(const EnvEntry &e, const mdp_request &r) {
 // arrays, R, cell classes, offsets, deferred-slice list, the compacted pool and
 // its scan while the first pool is still live), its solve (status words, the
 // Jacobi partner vector and layer flags) and the request's own V and policy,
-// each rounded up to 4 KiB, plus 1 MiB.
-int64_t charge_bytes(const EnvEntry &e, const mdp_request &r, uint64_t pool_cols) {
+// each rounded up to 4 KiB, plus 1 MiB; with spill_words > 0 also a spill area
+// of that many words and its per-slice offsets.
+int64_t charge_bytes(const EnvEntry &e, const mdp_request &r, uint64_t pool_cols, uint64_t spill_words) {
   const ReqShape g = req_shape(e, r);
   auto al = [](int64_t x) { return (x + 4095) & ~(int64_t)4095; };
   const int64_t max_sweeps = g.nt + 1;
@@ -143,6 +145,7 @@ int64_t charge_bytes(const EnvEntry &e, const mdp_request &r, uint64_t pool_cols
   b += al(8 * (4 + 2 * max_sweeps + (3 * (g.nt + 1) + 7) / 8 + 1));                           // solve status
   b += 3 * al(4 * (g.nS + 1)) + al(2 * g.nS);                                                  // V, partner, policy
   b += al((int64_t)e.grid.nx * e.grid.ny);                                                     // target mask
+  if (spill_words) b += al(4 * g.n_slices) + al(4 * (int64_t)spill_words);                     // spill area
   return b + (1 << 20);
 }
 
@@ -166,8 +169,10 @@ __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0
   }
 }
 
-// Returns true when the request must be charged again for a larger pool
-// (job.pool_cols then holds the exact need).
+// Returns true when the request must be charged again for a larger pool or
+// for a spill area (job.pool_cols / job.spill_words then hold the exact need;
+// a request is first charged without a spill area, which only rows longer
+// than the row cap -- wide, high-sigma fields -- need).
 bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   const EnvEntry &e = *S->envs[job.req.env_id];
   const mdp_request &r = job.req;
@@ -197,9 +202,12 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   mdp_model m = nullptr;
   BuildLimits lim;
   lim.pool_cols = job.pool_cols;
+  lim.spill_words = job.spill_words;
   mdp_status s = build_impl(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m, nullptr, &lim);
-  if (s == MDP_ERR_BUDGET && lim.pool_cols_needed > job.pool_cols) {
-    job.pool_cols = lim.pool_cols_needed;
+  if (s == MDP_ERR_BUDGET &&
+      (lim.pool_cols_needed > job.pool_cols || lim.spill_words_needed > job.spill_words)) {
+    job.pool_cols = std::max(job.pool_cols, lim.pool_cols_needed);
+    job.spill_words = std::max(job.spill_words, lim.spill_words_needed);
     cudaStreamSynchronize(st);
     return true;
   }
@@ -211,7 +219,7 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   {   // the model is compacted: the request now holds at most the charge of a
       // pool of the columns in use (the rest of its charge goes back)
     std::lock_guard<std::mutex> lk(S->mu);
-    const int64_t now = charge_bytes(e, job.req, std::max<uint64_t>(m->pool_cols, 1));
+    const int64_t now = charge_bytes(e, job.req, std::max<uint64_t>(m->pool_cols, 1), m->spill ? job.spill_words : 0);
     if (now < job.bytes) {
       S->bytes_in_use -= job.bytes - now;
       job.bytes = now;
@@ -347,7 +355,7 @@ void worker_main(mdp_server_t *S) {
         // the slices need a larger pool: charge the exact need and put the
         // request back at the head of the queue (or refuse it if the whole
         // budget is too small)
-        job->bytes = charge_bytes(e, job->req, job->pool_cols);
+        job->bytes = charge_bytes(e, job->req, job->pool_cols, job->spill_words);
         job->peak_bytes = std::max(job->peak_bytes, job->bytes);
         if (job->bytes > (int64_t)S->budget) {
           job->status = MDP_ERR_BUDGET;
@@ -488,10 +496,10 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   auto job = std::make_shared<Job>();
   job->req = *req;
   job->pool_cols = pool_worst(e, *req);
-  job->bytes = charge_bytes(e, *req, job->pool_cols);
+  job->bytes = charge_bytes(e, *req, job->pool_cols, 0);
   if (job->bytes > (int64_t)S->budget) {   // too much for the budget: the widths seen so far
     job->pool_cols = pool_guess(e, *req);
-    job->bytes = charge_bytes(e, *req, job->pool_cols);
+    job->bytes = charge_bytes(e, *req, job->pool_cols, 0);
   }
   job->peak_bytes = job->bytes;
   if (job->bytes > (int64_t)S->budget) {

@@ -57,7 +57,8 @@ class MdpModelInfo(C.Structure):
                 ("rows", C.c_int64), ("nnz", C.c_int64), ("max_row_nnz", C.c_int32),
                 ("pool_columns", C.c_int64), ("device_bytes", C.c_int64), ("samples", C.c_int64),
                 ("build_ms", C.c_double), ("kernel_ms", C.c_double), ("launches", C.c_int32),
-                ("wide_slices", C.c_int64), ("nnz_domain", C.c_int64)]
+                ("wide_slices", C.c_int64), ("nnz_domain", C.c_int64), ("spill_rows", C.c_int64),
+                ("spill_words", C.c_int64), ("max_row_len", C.c_int32)]
 
 
 class MdpSolveStats(C.Structure):

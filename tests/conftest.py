@@ -51,6 +51,29 @@ def custom_env(nx=7, ny=7, nt=5, K=1, N=64, L=5, vbar=None, modes=None, sigma=No
                               gbar=gbar, Y=Y, **kw)
 
 
+def device_pool_meter():
+    """(reset the high-water mark, read (used now, high-water mark)) of the
+    current device's default memory pool, through the CUDA driver API."""
+    import ctypes as C
+    cu = C.CDLL("libcuda.so.1")
+    dev = C.c_int()
+    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    USED, USED_HIGH = 7, 8   # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
+
+    def reset():
+        zero = C.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, C.byref(zero)) == 0
+
+    def read():
+        a, b = C.c_uint64(), C.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, USED, C.byref(a)) == 0
+        assert cu.cuMemPoolGetAttribute(pool, USED_HIGH, C.byref(b)) == 0
+        return a.value, b.value
+    return reset, read
+
+
 @pytest.fixture
 def make_env():
     return custom_env

@@ -6,7 +6,7 @@ import time
 import numpy as np
 import pytest
 
-from conftest import oracle_end_to_end
+from conftest import device_pool_meter, oracle_end_to_end
 from paper_2109_00857_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -230,29 +230,6 @@ def _wide_env():
     return custom_env(nx=9, ny=9, nt=nt, K=2, N=3000, L=15, seed=12, sigma=[1.1, 1.0], modes=modes)
 
 
-def _pool_used():
-    """(reset high-water mark, read (used now, high-water mark)) of the
-    device's default memory pool, through the CUDA driver API."""
-    import ctypes as C
-    cu = C.CDLL("libcuda.so.1")
-    dev = C.c_int()
-    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
-    pool = C.c_void_p()
-    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
-    USED, USED_HIGH = 7, 8   # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
-
-    def reset():
-        zero = C.c_uint64(0)
-        assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, C.byref(zero)) == 0
-
-    def read():
-        a, b = C.c_uint64(), C.c_uint64()
-        assert cu.cuMemPoolGetAttribute(pool, USED, C.byref(a)) == 0
-        assert cu.cuMemPoolGetAttribute(pool, USED_HIGH, C.byref(b)) == 0
-        return a.value, b.value
-    return reset, read
-
-
 def _charges(mdp, env, kw):
     """(charge of the largest possible pool, charge of the exact pool) of a
     request: the first from a server with room for it, the second from a
@@ -282,7 +259,7 @@ def test_a_request_never_holds_more_device_memory_than_it_was_charged(mdp):
     stopped at that pool, charged again for the exact need and rerun -- and the
     result equals a direct build + solve."""
     import torch
-    reset, read = _pool_used()
+    reset, read = device_pool_meter()
     for env, kw in ((_env(), dict(start=(3, 4), target=(20, 20), seed=5, N=300, objective=1)),
                     (_wide_env(), dict(start=(4, 4), target=(1, 1), seed=7, N=3000, objective=0))):
         worst, exact = _charges(mdp, env, kw)
