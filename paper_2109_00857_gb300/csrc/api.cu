@@ -365,10 +365,13 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   double *sig_d = nullptr;
   TRY(dev_alloc((void **)&m->cnt, sizeof(unsigned long long) * CNT_N, st));
   TRY(cudaMemsetAsync(m->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
-  cudaEvent_t ev0, ev1, evk;
-  cudaEventCreate(&ev0);
-  cudaEventCreate(&ev1);
-  cudaEventCreate(&evk);
+  // timing events, destroyed on every return path
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    Events() { for (auto &x : e) cudaEventCreate(&x); }
+    ~Events() { for (auto &x : e) if (x) cudaEventDestroy(x); }
+  } evs;
+  cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1], evk = evs.e[2];
   cudaEventRecord(ev0, st);
   int launches = 0;
   if (!Y && env->K > 0) {
@@ -470,6 +473,7 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   ba.pool = m->pool; ba.pool_cap_cols = cap_cols; ba.slice_off = m->slice_off; ba.slice_w = m->slice_w; ba.nnz = m->nnz; ba.sinkc = m->sinkc;
   ba.R = m->R; ba.cnt = m->cnt;
   ba.slice_begin = 0; ba.slice_end = m->n_slices;
+  ba.slices_per_warp = lim ? lim->slices_per_warp : 0;
   // spill area: the caller's size when it fixes the pool (the server), else none yet
   uint64_t spill_cap = (lim && lim->pool_cols) ? lim->spill_words : 0;
   auto alloc_spill = [&](uint64_t words) -> cudaError_t {
@@ -492,7 +496,18 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   if (threads % 64 != 0 || threads > 512) return fail(arg_fail("threads must be a multiple of 64, <= 512"));
   int chunk = (opts && opts->chunk > 0) ? opts->chunk : tun.chunk;
   if (chunk > N) chunk = N;
+  // the full-window kernels hold an [L*L][32] histogram in shared memory: the
+  // FP32 one halves its realization chunk until it fits (the model does not
+  // depend on the chunk); beyond that (sub-grids above 41 x 41 cells) only
+  // the warp kernel's slices can be built
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
+  const size_t window_limit = (size_t)smem_max - 1024;   // the kernels' static shared memory
+  if (prec == MDP_FP64_CHECK && (size_t)m->nbins * 128 > window_limit)
+    return fail(arg_fail("check mode needs a sub-grid of at most 41 x 41 cells (its histogram is in shared memory)"));
   ba.chunk = chunk;
+  while (chunk > 32 && fp32_smem_bytes(ba, threads) > window_limit) ba.chunk = chunk = chunk / 2;
+  const bool window_fits = fp32_smem_bytes(ba, threads) <= window_limit;
   int hist_cap = (opts && opts->hist_cap > 0) ? opts->hist_cap : tun.hist_cap;
   const int build_warps = tun.build_warps;
   if (hist_cap > 6144) return fail(arg_fail("hist_cap must be <= 6144"));
@@ -502,9 +517,6 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   ba.defer = defer;
   ba.defer_in = nullptr;
   if (hook) {
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    cudaEventDestroy(evk);
     hook->args = ba;
     hook->Yown = Yown;
     hook->sigma_d = sig_d;
@@ -527,8 +539,8 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
       TRY(launch_build_warp(ba, build_warps, num_sms(), st));
       BuildArgs bd = ba;
       bd.defer_in = defer;
-      TRY(launch_build_fp32(bd, threads, num_sms(), st));
-      launches += 2;
+      if (window_fits) TRY(launch_build_fp32(bd, threads, num_sms(), st));
+      launches += window_fits ? 2 : 1;
     }
     cudaEventRecord(ev1, st);
     TRY(cudaMemcpyAsync(pin.p, m->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
@@ -553,9 +565,6 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
       if (Yown) dev_free(Yown, st);
       if (sig_d) dev_free(sig_d, st);
       if (defer) dev_free(defer, st);
-      cudaEventDestroy(ev0);
-      cudaEventDestroy(ev1);
-      cudaEventDestroy(evk);
       return fail(MDP_ERR_BUDGET);
     }
     // does not fit the device (or the 32-bit block offsets): reported as MDP_ERR_OOM below
@@ -578,15 +587,21 @@ mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_action
   if (sig_d) dev_free(sig_d, st);
   if (defer) dev_free(defer, st);
   m->deferred = (int64_t)c[CNT_DEFER_N];
+
   float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventElapsedTime(&kms, evk, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
-  cudaEventDestroy(evk);
   m->build_ms = ms;
   m->kernel_ms = kms;
   m->launches = launches;
+  if (prec == MDP_FP32 && !window_fits && m->deferred > 0) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "%lld slice(s) need the full-window kernel, whose histogram of a %dx%d sub-grid "
+             "exceeds shared memory: raise hist_cap or use a sub-grid of at most 41 x 41 cells",
+             (long long)m->deferred, L, L);
+    set_error(buf);
+    return fail(MDP_ERR_ARG);
+  }
   if (c[CNT_OVERFLOW]) {
     char buf[256];
     snprintf(buf, sizeof buf, "%llu landing(s)/row(s) left the %dx%d neighbouring sub-grid; use a larger subgrid_L",
@@ -751,6 +766,7 @@ static mdp_status solve_impl(mdp_model m, int32_t n, const int32_t *objs, int32_
   a.wcap = std::max(1, m->max_row_nnz);
   a.spill = m->spill;
   a.spill_off = m->spill_off;
+  a.small_ctas = m->sweep_small_ctas;
   a.R = io.R[0];
   a.cls = m->cls; a.delta = m->delta;
   a.nS = m->nS; a.Nc = m->Nc; a.n_slices = m->n_slices;

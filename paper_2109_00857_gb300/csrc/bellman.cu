@@ -1310,7 +1310,7 @@ static int ws_entry_bytes(int wcap, int smem_kb) {
 template <typename RT, int NO>
 static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr, size_t *smem, int *blocks) {
   pr->dtab_smem = 0;
-  if (a.spw == 1) {   // one state per slice: the warp-specialized sweep, any width
+  if (a.spw == 1 && !a.small_ctas) {   // one state per slice: the warp-specialized sweep, any width
     pr->grouped = 2;
     pr->stage_bytes = ws_entry_bytes<RT, NO>(a.wcap, a.sweep_smem_kb);
     *smem = ws_hdr_bytes() + ws_old_bytes<RT, NO>() + (size_t)kWsSlots * (ws_r_bytes<RT>(NO) + pr->stage_bytes);

@@ -1,11 +1,15 @@
 // build_warp.cu -- production FP32 MDP build, warp-per-slice fast path
 // (single-model kernel and launchers; the slice algorithm is in build_warp.cuh,
 // the batched kernel in build_warp_batch.cu).
+#include <algorithm>
+
 #include "build_warp.cuh"
 
 namespace mdpgb {
 
-// Single model: persistent warps pull slices from the model's work queue.
+// Single model: warps pull slices from the model's work queue -- persistent
+// warps, or at most a.slices_per_warp slices each (the grid then covers the
+// model: capacity blocks x warps x q >= slices, so every slice is taken).
 template <int KT, int SPW>
 __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -16,10 +20,12 @@ __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
   WarpAcc acc;
   unsigned long long next = 0;
   if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);
-  for (;;) {
+  for (int n = 1;; ++n) {
     const int64_t sl = a.slice_begin + (int64_t)__shfl_sync(0xffffffffu, next, 0);
     if (sl >= a.slice_end) break;
-    if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);   // prefetch the next slice
+    // prefetch the next slice, unless this warp's share ends with this one
+    const bool more = a.slices_per_warp == 0 || n < a.slices_per_warp;
+    if (lane == 0) next = more ? atomicAdd(&a.cnt[CNT_WORK], 1ULL) : (unsigned long long)(a.slice_end - a.slice_begin);
     warp_slice<KT, SPW>(a, sl, grid, tab, acc);
     __syncwarp();
   }
@@ -39,6 +45,10 @@ static cudaError_t launch_w(const BuildArgs &a, int warps, int sms, cudaStream_t
   int64_t blocks = (int64_t)sms * per_sm;
   const int64_t need = (a.slice_end - a.slice_begin + warps - 1) / warps;
   if (blocks > need) blocks = need > 0 ? need : 1;
+  if (a.slices_per_warp > 0) {   // bounded warps: a grid that covers every slice
+    const int64_t per_cta = (int64_t)warps * a.slices_per_warp;
+    blocks = std::max<int64_t>(1, (a.slice_end - a.slice_begin + per_cta - 1) / per_cta);
+  }
   build_warp_kernel<KT, SPW><<<(unsigned)blocks, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -109,6 +109,31 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
   return make_float2(ux, uy);
 }
 
+// The same velocity from a coefficient row already loaded (KT a multiple of
+// 4): the identical FMA chain, so both forms give the same u bit for bit.
+template <int KT>
+__device__ __forceinline__ void load_row4(const float *__restrict__ yw, float4 (&y)[KT / 4]) {
+#pragma unroll
+  for (int v = 0; v < KT / 4; ++v) y[v] = __ldg(reinterpret_cast<const float4 *>(yw) + v);
+}
+template <int KT>
+__device__ __forceinline__ float2 velocity_row4(const float4 (&y)[KT / 4], const float (&phx)[kPhi<KT>],
+                                                const float (&phy)[kPhi<KT>], float vbx, float vby, float lam) {
+  float wx = vbx, wy = vby;
+#pragma unroll
+  for (int v = 0; v < KT / 4; ++v) {
+    const int k = 4 * v;
+    wx = fmaf(y[v].x, phx[k], wx); wy = fmaf(y[v].x, phy[k], wy);
+    wx = fmaf(y[v].y, phx[k + 1], wx); wy = fmaf(y[v].y, phy[k + 1], wy);
+    wx = fmaf(y[v].z, phx[k + 2], wx); wy = fmaf(y[v].z, phy[k + 2], wy);
+    wx = fmaf(y[v].w, phx[k + 3], wx); wy = fmaf(y[v].w, phy[k + 3], wy);
+  }
+  float ux = fmaf(wx, lam, 0.5f), uy = fmaf(wy, lam, 0.5f);
+  if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
+  if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+  return make_float2(ux, uy);
+}
+
 // Rank tables of one axis in a warp's table memory.
 struct RankTab {
   const float2 *TP;    // TP[i] = (T[i], T[i+1]); T[i] = 2 for i >= D
@@ -324,14 +349,29 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     // ---- pass 2: one count per realization in its state's fine table
     if (kind_t == KIND_SAMPLE) {
       const uint32_t gbase = smem_u32(grid + gt.base);
-#pragma unroll 1
-      for (int w = wi; w < N; w += wstep) {
-        const float2 u = velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam);
+      auto count = [&](float2 u) {
         int X = fine_coord(u.x, gt.n0x, Sx, rx) - gt.xmin;
         int Y = fine_coord(u.y, gt.n0y, Sy, ry) - gt.ymin;
         X = min(max(X, 0), gt.gx - 1);
         Y = min(max(Y, 0), gt.gy - 1);
         red_add_shared(gbase + 4u * (uint32_t)((X + 1) * gt.pitch + Y + 1), 1u);
+      };
+      if constexpr (KT > 0 && KT % 4 == 0) {
+        // the next realization's coefficient row is loaded while this one
+        // is counted (its L2 latency overlaps the rank lookups)
+        float4 yn[KT / 4];
+        if (wi < N) load_row4<KT>(Yt + (size_t)wi * K, yn);
+#pragma unroll 1
+        for (int w = wi; w < N; w += wstep) {
+          float4 yc[KT / 4];
+#pragma unroll
+          for (int v = 0; v < KT / 4; ++v) yc[v] = yn[v];
+          if (w + wstep < N) load_row4<KT>(Yt + (size_t)(w + wstep) * K, yn);
+          count(velocity_row4<KT>(yc, phx, phy, vbx, vby, lam));
+        }
+      } else {
+#pragma unroll 1
+        for (int w = wi; w < N; w += wstep) count(velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam));
       }
     }
     __syncwarp();

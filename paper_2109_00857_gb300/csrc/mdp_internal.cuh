@@ -125,6 +125,11 @@ struct BuildArgs {
   uint32_t *spill;
   uint32_t *spill_off;       // [n_slices] word offset of the slice's block, or kNoSlice
   uint64_t spill_cap_words;
+  // single-model warp kernel: 0 = persistent warps (one CTA wave pulls every
+  // slice); q > 0 = each warp builds at most q slices and the grid covers the
+  // model, so CTAs retire all along the build and the block scheduler can
+  // place higher-priority work (another request's launches) between them
+  int32_t slices_per_warp;
 };
 
 struct mdp_model_impl;
@@ -170,6 +175,7 @@ struct mdp_model_t {
   int64_t spill_rows;         // rows with entries beyond row_cap
   int64_t spill_entries;      // entries held in the spill blocks
   int32_t max_row_len;        // longest row (in-domain successors + sink)
+  int32_t sweep_small_ctas;   // 1: sweeps use CTAs that share an SM with other work (the server)
 };
 
 namespace mdpgb {
@@ -239,6 +245,7 @@ struct SolveArgs {
   uint32_t test_extra_tx = 0; // failure injection (tests): bytes one wait expects that never arrive
   const uint32_t *spill = nullptr;      // HYB spill blocks (nullptr: the model has none)
   const uint32_t *spill_off = nullptr;  // [n_slices]
+  int32_t small_ctas = 0;     // 1: the warp-per-slice sweep also for one state per slice
 };
 // Launch shapes chosen by the autotuner (mdp_autotune) per workload class;
 // every choice gives the same model and values bit for bit.
@@ -346,6 +353,7 @@ struct BuildLimits {
   uint64_t pool_cols_needed = 0;   // out (MDP_ERR_BUDGET): the columns the slices need
   uint64_t spill_words = 0;        // in (with pool_cols): spill words to allocate (0: none)
   uint64_t spill_words_needed = 0; // out (MDP_ERR_BUDGET): the spill words the rows need
+  int32_t slices_per_warp = 0;     // in: BuildArgs::slices_per_warp of the warp kernel
 };
 mdp_status build_impl(const mdp_env *env, const mdp_grid *grid, const mdp_actions *actions, int32_t N,
                       int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj, const mdp_build_opts *opts,

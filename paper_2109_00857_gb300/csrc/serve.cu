@@ -169,6 +169,9 @@ __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0
   }
 }
 
+// slices per build warp when requests share the GPU (BuildArgs::slices_per_warp)
+constexpr int kServeSlicesPerWarp = 8;
+
 // Returns true when the request must be charged again for a larger pool or
 // for a spill area (job.pool_cols / job.spill_words then hold the exact need;
 // a request is first charged without a spill area, which only rows longer
@@ -203,6 +206,16 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   BuildLimits lim;
   lim.pool_cols = job.pool_cols;
   lim.spill_words = job.spill_words;
+  // While other requests run, kernels that leave the SMs all along their run:
+  // the build's warps take a few slices each and the sweeps use small CTAs, so
+  // the stream priorities (older requests first) decide whose blocks run next
+  // instead of one launch holding every SM to its end.  A request alone on
+  // the GPU takes the faster persistent kernels.
+  auto others_running = [&] {
+    std::lock_guard<std::mutex> lk(S->mu);
+    return S->running.size() > 1;
+  };
+  lim.slices_per_warp = others_running() ? kServeSlicesPerWarp : 0;
   mdp_status s = build_impl(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m, nullptr, &lim);
   if (s == MDP_ERR_BUDGET &&
       (lim.pool_cols_needed > job.pool_cols || lim.spill_words_needed > job.spill_words)) {
@@ -235,6 +248,7 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
     if (!S->envs[job.req.env_id]->cols_seen || need > c) c = std::max(2.0, need);
     S->envs[job.req.env_id]->cols_seen = true;
   }
+  m->sweep_small_ctas = others_running() ? 1 : 0;
   const int64_t nS = m->nS;
   float *V = nullptr;
   int16_t *pi = nullptr;
