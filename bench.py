@@ -432,8 +432,7 @@ def run_cube(args):
                          "solve": statistics.mean(solve_ms)},
             "sweeps": [s.sweeps for s in rec["stats"]],
             "roofline": roof_build, "roofline_build": roof_build,
-            "roofline_bellman": {"kernel": "bellman_kernel_g" if env.A > 16 and info.max_row_nnz <= 13
-                                 else "bellman_kernel", "bound": "hbm", "achieved": bell, "peak": hbm,
+            "roofline_bellman": {"kernel": "bellman_kernel_ws" if env.A > 16 else "bellman_kernel", "bound": "hbm", "achieved": bell, "peak": hbm,
                                  "unit": "GB/s", "frac": bell / hbm, "bytes_per_sweep": bpsw,
                                  "ms_per_sweep": sweep_ms, "peak_basis": f"hbm_gbs ({peak_kind})"},
             "gpu_launches": launches, "clocks": clocks, "tuning": tuning,
@@ -773,8 +772,8 @@ def main():
                   "counters": cb["summary"] if cb else "stale or absent: kernel changed since the capture",
                   "ms_per_launch": kmean,
                   "peak_basis": f"{sms} SMs x 4 issue slots x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})"}
-    # the ring sweep serves one-state slices (A_pad = 32)
-    bell_name = "bellman_kernel_r" if env.A > 16 else "bellman_kernel"
+    # the warp-specialized sweep serves one-state slices (A_pad = 32)
+    bell_name = "bellman_kernel_ws" if env.A > 16 else "bellman_kernel"
     roof_bell = {"kernel": bell_name, "objectives_per_sweep": n_fused, "bound": "hbm",
                  "achieved": bell_achieved, "peak": hbm, "unit": "GB/s", "frac": bell_achieved / hbm,
                  "traffic": cs["dram_bytes_per_unit"] * n_slices if cs else None,

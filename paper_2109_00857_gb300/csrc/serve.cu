@@ -92,7 +92,13 @@ struct mdp_server_t {
   size_t budget = 0;
   int slots = 1;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
+  // idle workers wait on their own condition variable; a request wakes the
+  // most recently idle one (its streams and buffers are warm), so a request
+  // alone on the server runs like the one-slot server, and no other worker
+  // is woken for nothing
+  std::vector<std::unique_ptr<std::condition_variable>> wcv;
+  std::vector<int> idle;
   std::deque<std::shared_ptr<Job>> queue;
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   std::vector<std::unique_ptr<EnvEntry>> envs;
@@ -108,6 +114,22 @@ struct mdp_server_t {
 namespace {
 
 // Geometry of a request's model: the remaining horizon's states and slices.
+// (S->mu held) wakes the most recently idle worker, or every idle worker
+void wake_one(mdp_server_t *S) {
+  if (S->idle.empty()) return;
+  const int j = S->idle.back();
+  S->idle.pop_back();
+  S->wcv[j]->notify_one();
+}
+void wake_all(mdp_server_t *S) {
+  for (int j : S->idle) S->wcv[j]->notify_one();
+  S->idle.clear();
+}
+// (S->mu held) the queue's head may start now
+bool head_fits(const mdp_server_t *S) {
+  return !S->queue.empty() && S->bytes_in_use + S->queue.front()->bytes <= (int64_t)S->budget;
+}
+
 struct ReqShape {
   int64_t nt, nS, n_slices, rows_pad, nbins;
 };
@@ -206,16 +228,16 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   BuildLimits lim;
   lim.pool_cols = job.pool_cols;
   lim.spill_words = job.spill_words;
-  // While other requests run, kernels that leave the SMs all along their run:
-  // the build's warps take a few slices each and the sweeps use small CTAs, so
-  // the stream priorities (older requests first) decide whose blocks run next
-  // instead of one launch holding every SM to its end.  A request alone on
-  // the GPU takes the faster persistent kernels.
-  auto others_running = [&] {
+  // The oldest running request takes the fastest (persistent) kernels.  A
+  // younger one runs beside it with kernels that leave the SMs all along
+  // their run -- the build's warps take a few slices each and the sweeps use
+  // small CTAs -- so the stream priorities (older first) decide whose blocks
+  // run next: the younger request fills the SMs the older one leaves idle.
+  auto younger = [&] {
     std::lock_guard<std::mutex> lk(S->mu);
-    return S->running.size() > 1;
+    return !S->running.empty() && S->running.front().get() != &job;
   };
-  lim.slices_per_warp = others_running() ? kServeSlicesPerWarp : 0;
+  lim.slices_per_warp = younger() ? kServeSlicesPerWarp : 0;
   mdp_status s = build_impl(&env, &grid, &e.actions, r.N, e.L, &obj, 1, nullptr, st, &m, nullptr, &lim);
   if (s == MDP_ERR_BUDGET &&
       (lim.pool_cols_needed > job.pool_cols || lim.spill_words_needed > job.spill_words)) {
@@ -237,8 +259,8 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
       S->bytes_in_use -= job.bytes - now;
       job.bytes = now;
     }
+    if (head_fits(S)) wake_one(S);
   }
-  S->cv_work.notify_all();
   {   // the widest pool per slice this environment's requests have needed (with
       // 10 % to spare) prices the next ones: widths vary with sigma and N, and
       // a charge that is too small costs the request a second build
@@ -248,7 +270,7 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
     if (!S->envs[job.req.env_id]->cols_seen || need > c) c = std::max(2.0, need);
     S->envs[job.req.env_id]->cols_seen = true;
   }
-  m->sweep_small_ctas = others_running() ? 1 : 0;
+  m->sweep_small_ctas = younger() ? 1 : 0;
   const int64_t nS = m->nS;
   float *V = nullptr;
   int16_t *pi = nullptr;
@@ -307,7 +329,7 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   return false;
 }
 
-void worker_main(mdp_server_t *S) {
+void worker_main(mdp_server_t *S, int id) {
   cudaSetDevice(S->device);
   // one stream per priority level; a request runs on the level it got at admission
   std::vector<cudaStream_t> streams(S->prio_levels);
@@ -321,10 +343,12 @@ void worker_main(mdp_server_t *S) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       // FIFO admission: the head waits until its charge fits the budget
-      S->cv_work.wait(lk, [&] {
-        return S->stopping || (!S->queue.empty() &&
-                               S->bytes_in_use + S->queue.front()->bytes <= (int64_t)S->budget);
-      });
+      while (!S->stopping && !head_fits(S)) {
+        S->idle.push_back(id);
+        S->wcv[id]->wait(lk);
+        auto it = std::find(S->idle.begin(), S->idle.end(), id);   // a spurious wake-up
+        if (it != S->idle.end()) S->idle.erase(it);
+      }
       if (S->stopping) break;
       job = S->queue.front();
       S->queue.pop_front();
@@ -334,6 +358,7 @@ void worker_main(mdp_server_t *S) {
       // priority by age: behind the requests still running
       job->level = std::min<int>((int)S->running.size(), S->prio_levels - 1);
       S->running.push_back(job);
+      if (head_fits(S)) wake_one(S);   // the next request may start beside this one
     }
     cudaStream_t st = streams[job->level];
     const EnvEntry &e = *S->envs[job->req.env_id];
@@ -388,8 +413,7 @@ void worker_main(mdp_server_t *S) {
         job->done = true;
       }
     }
-    S->cv_done.notify_all();
-    S->cv_work.notify_all();
+    S->cv_done.notify_all();   // this worker itself takes the next request, if any
   }
   dev_free(tgt, tst);
   for (cudaStream_t x : streams) {
@@ -425,7 +449,8 @@ extern "C" mdp_status mdp_serve_create(size_t hbm_budget_bytes, int32_t max_slot
     S->prio_greatest = greatest;
     S->prio_levels = std::min(least - greatest + 1, max_slots);
   }
-  for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
+  for (int i = 0; i < max_slots; ++i) S->wcv.emplace_back(new std::condition_variable());
+  for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S, i);
   *out = S;
   return MDP_OK;
 }
@@ -525,7 +550,7 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   S->jobs[job->ticket] = job;
   S->queue.push_back(job);
   *ticket = job->ticket;
-  S->cv_work.notify_all();
+  if (head_fits(S)) wake_one(S);
   return MDP_OK;
 }
 
@@ -588,7 +613,10 @@ extern "C" mdp_status mdp_serve_destroy(mdp_server S) {
     }
     S->queue.clear();
   }
-  S->cv_work.notify_all();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    wake_all(S);
+  }
   S->cv_done.notify_all();
   for (auto &t : S->workers) t.join();
   cudaSetDevice(S->device);
