@@ -435,7 +435,7 @@ def run_cube(args):
             "roofline_bellman": {"kernel": "bellman_kernel_ws" if env.A > 16 else "bellman_kernel", "bound": "hbm", "achieved": bell, "peak": hbm,
                                  "unit": "GB/s", "frac": bell / hbm, "bytes_per_sweep": bpsw,
                                  "ms_per_sweep": sweep_ms, "peak_basis": f"hbm_gbs ({peak_kind})"},
-            "gpu_launches": launches, "clocks": clocks, "tuning": tuning,
+            "gpu_launches": launches, "clocks": clocks, "tuning": None,
             "model": {"nnz": info.nnz, "rows": info.rows, "max_row_nnz": info.max_row_nnz,
                       "device_bytes": info.device_bytes}}
     if not args.no_cpu_baseline:
