@@ -753,19 +753,26 @@ __device__ __forceinline__ void bellman_body_g(const SolveArgs &a, const VSet<RT
 // ballot (FP64: a butterfly): values and policy equal theirs bit for bit.
 constexpr int kWsCons = 31;     // consumer warps per CTA (+ 1 producer = 1024 threads)
 constexpr int kWsSlots = 3;     // round slots
+// slices per consumer warp and round (warp w takes slices w, w + 31, ...;
+// its slices' column loops run interleaved).  Measured on the large
+// workload: 1 (rounds of 31 slices in three slots) 99.5 ms per solve, 2
+// (rounds of 62 in two slots) 108-117 ms.
+constexpr int kWsPer = 1;
+constexpr int kWsRound = kWsCons * kWsPer;   // most slices in a round
+constexpr int kWsTab = 32 * kWsPer;          // table entries per slot
 
 struct WsHdr {
   uint64_t full[kWsSlots];      // producer arrival + the round's copied bytes
   uint64_t empty[kWsSlots];     // one arrival per consumer warp
   int2 round[kWsSlots];         // (first slice, slices in the round); 0 slices ends the block
-  int2 slice[kWsSlots][32];     // (entry byte offset in the slot, W | cell class << 8) per slice
+  int2 slice[kWsSlots][kWsTab]; // (entry byte offset in the slot, W | cell class << 8) per slice
 };
 __host__ __device__ constexpr size_t ws_hdr_bytes() { return (sizeof(WsHdr) + 127) & ~(size_t)127; }
-// the slices' current values, [kWsSlots][32]
+// the slices' current values, [kWsSlots][kWsTab]
 template <typename RT, int NO>
-__host__ __device__ constexpr size_t ws_old_bytes() { return (kWsSlots * 32 * sizeof(VPack<RT, NO>) + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t ws_old_bytes() { return (kWsSlots * kWsTab * sizeof(VPack<RT, NO>) + 127) & ~(size_t)127; }
 template <typename RT>
-__host__ __device__ constexpr int ws_r_bytes(int n_obj) { return n_obj * 32 * 32 * (int)sizeof(RT); }
+__host__ __device__ constexpr int ws_r_bytes(int n_obj) { return n_obj * kWsTab * 32 * (int)sizeof(RT); }
 
 template <typename RT, int NO>
 __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
@@ -813,21 +820,24 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
       if (lane == o) myR = v.R[o];
     int64_t sl = b_lo;
     bool failed = false;
-    // lane l: slice sl + l of the next round -- pool column, columns, cell
+    // lane l: slices sl + l + 32 i of the next round -- pool column, columns, cell
     // class and current values -- loaded before the wait for its slot
-    uint32_t off = 0;
-    int W = 0, cls = 0;
-    Pk old{};
+    uint32_t off[kWsPer];
+    int W[kWsPer], cls[kWsPer];
+    Pk old[kWsPer];
     auto fetch = [&]() {
-      off = 0;
-      W = 0;
-      cls = 0;
-      if (lane < kWsCons && sl + lane < b_hi) {
-        const int64_t x = sl + lane;
-        off = __ldg(a.slice_off + x);
-        W = __ldg(a.slice_w + x);
-        cls = __ldg(a.cls + x);   // spw = 1: state = slice
-        old = v.in[x];
+#pragma unroll
+      for (int i = 0; i < kWsPer; ++i) {
+        off[i] = 0;
+        W[i] = 0;
+        cls[i] = 0;
+        if (lane + 32 * i < kWsRound && sl + lane + 32 * i < b_hi) {
+          const int64_t x = sl + lane + 32 * i;
+          off[i] = __ldg(a.slice_off + x);
+          W[i] = __ldg(a.slice_w + x);
+          cls[i] = __ldg(a.cls + x);   // spw = 1: state = slice
+          old[i] = v.in[x];
+        }
       }
     };
     fetch();
@@ -839,22 +849,33 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
         failed = true;
         break;
       }
-      int n = 0, tot = 0, e = 0;
-      const uint32_t off0 = __shfl_sync(0xffffffffu, off, 0);
-      if (sl < b_hi) {
-        int cum = W * 128;   // inclusive scan of the entry bytes
+      int n = 0, tot = 0, e[kWsPer];
+      const uint32_t off0 = __shfl_sync(0xffffffffu, off[0], 0);
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int x = __shfl_up_sync(0xffffffffu, cum, d);
-          if (lane >= d) cum += x;
-        }
-        const bool valid = lane < kWsCons && sl + lane < b_hi;
-        n = __popc(__ballot_sync(0xffffffffu, valid && cum <= ecap));   // a prefix of the lanes
-        tot = __shfl_sync(0xffffffffu, cum, (n > 0 ? n : 1) - 1);
-        e = cum - W * 128;
-        if (lane < n) {
-          hdr->slice[slot][lane] = make_int2(e, W | (cls << 8));
-          olds[slot * 32 + lane] = old;
+      for (int i = 0; i < kWsPer; ++i) e[i] = 0;
+      if (sl < b_hi) {
+        int carry = 0;
+        bool open = true;
+#pragma unroll
+        for (int i = 0; i < kWsPer; ++i) {
+          int cum = W[i] * 128;   // inclusive scan of the entry bytes
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, cum, d);
+            if (lane >= d) cum += x;
+          }
+          cum += carry;
+          const bool valid = open && lane + 32 * i < kWsRound && sl + lane + 32 * i < b_hi;
+          const int ni = __popc(__ballot_sync(0xffffffffu, valid && cum <= ecap));   // a prefix of the lanes
+          if (ni > 0) tot = __shfl_sync(0xffffffffu, cum, ni - 1);
+          e[i] = cum - W[i] * 128;
+          if (lane < ni) {
+            hdr->slice[slot][32 * i + lane] = make_int2(e[i], W[i] | (cls[i] << 8));
+            olds[slot * kWsTab + 32 * i + lane] = old[i];
+          }
+          n += ni;
+          if (ni < 32) open = false;
+          carry = __shfl_sync(0xffffffffu, cum, 31);
         }
       }
       __syncwarp();   // the slot's table is written before lane 0 arrives (release)
@@ -880,14 +901,19 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           bulk_g2s_stream(sbase + (uint32_t)kRBytes, a.pool + (size_t)off0 * 32, (uint32_t)tot, fb, stream_policy);
         }
-      } else if (lane < n && W > 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_g2s_stream(sbase + (uint32_t)(kRBytes + e), a.pool + (size_t)off * 32, (uint32_t)W * 128u,
-                        fb, stream_policy);
+      } else {
+#pragma unroll
+        for (int i = 0; i < kWsPer; ++i) {
+          if (lane + 32 * i < n && W[i] > 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_g2s_stream(sbase + (uint32_t)(kRBytes + e[i]), a.pool + (size_t)off[i] * 32, (uint32_t)W[i] * 128u,
+                            fb, stream_policy);
+          }
+        }
       }
       if (lane < NO) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_g2s_stream(sbase + (uint32_t)(lane * 32 * kRB), myR + (size_t)sl * 32, (uint32_t)(n * kRB), fb,
+        bulk_g2s_stream(sbase + (uint32_t)(lane * kWsTab * kRB), myR + (size_t)sl * 32, (uint32_t)(n * kRB), fb,
                         stream_policy);
       }
       __syncwarp();
@@ -940,31 +966,46 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
       }
       const int2 rdesc = hdr->round[slot];
       if (rdesc.y == 0) break;
-      const bool mine = warp < rdesc.y;
-      const int s = rdesc.x + warp;   // spw = 1: state = slice
-      Acc<RT> acc[NO];
-      RT Rv[NO];
-      Pk old{};
-      int wc = 0;
-      if (mine) {
-        const int2 sd = hdr->slice[slot][warp];
-        wc = sd.y;
-        const int W = wc & 0xFF;
-        const unsigned char *sb = slots + (size_t)slot * slot_bytes;
-        const uint32_t *ent = reinterpret_cast<const uint32_t *>(sb + kRBytes + sd.x) + lane;
-        const int sn = (s + Nc <= nS) ? s + Nc : nS;
-        const Pk *Vn = v.in + sn;
-#pragma unroll 2
-        for (int kk = 0; kk < W; ++kk) {   // every column of the slice, ascending
-          const uint32_t w = ent[kk * 32];
-          const Pk g = Vn[(int)(int16_t)(w & 0xFFFFu)];
+      Acc<RT> accs[kWsPer][NO];
+      RT Rvs[kWsPer][NO];
+      Pk olds_i[kWsPer];
+      int wcs[kWsPer], Ws[kWsPer];
+      const uint32_t *ents[kWsPer];
+      const Pk *Vns[kWsPer];
+      const unsigned char *sb = slots + (size_t)slot * slot_bytes;
+      int Wm = 0;
 #pragma unroll
-          for (int o = 0; o < NO; ++o) acc[o].add(w >> 16, g.v[o], a.N);
+      for (int i = 0; i < kWsPer; ++i) {
+        const int j = warp + kWsCons * i;
+        Ws[i] = 0;
+        wcs[i] = 0;
+        ents[i] = nullptr;
+        Vns[i] = v.in;
+        if (j < rdesc.y) {
+          const int si = rdesc.x + j;
+          const int2 sd = hdr->slice[slot][j];
+          wcs[i] = sd.y;
+          Ws[i] = sd.y & 0xFF;
+          ents[i] = reinterpret_cast<const uint32_t *>(sb + kRBytes + sd.x) + lane;
+          Vns[i] = v.in + ((si + Nc <= nS) ? si + Nc : nS);
+          const RT *Rs = reinterpret_cast<const RT *>(sb) + j * 32 + lane;
+#pragma unroll
+          for (int o = 0; o < NO; ++o) Rvs[i][o] = Rs[o * kWsTab * 32];
+          olds_i[i] = olds[slot * kWsTab + j];
         }
-        const RT *Rs = reinterpret_cast<const RT *>(sb) + warp * 32 + lane;
+        Wm = max(Wm, Ws[i]);
+      }
+#pragma unroll 2
+      for (int kk = 0; kk < Wm; ++kk) {   // every column of each slice, ascending
 #pragma unroll
-        for (int o = 0; o < NO; ++o) Rv[o] = Rs[o * 32 * 32];
-        old = olds[slot * 32 + warp];
+        for (int i = 0; i < kWsPer; ++i) {
+          if (kk < Ws[i]) {
+            const uint32_t w = ents[i][kk * 32];
+            const Pk g = Vns[i][(int)(int16_t)(w & 0xFFFFu)];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) accs[i][o].add(w >> 16, g.v[o], a.N);
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8u * (uint32_t)slot);   // the slot is read
@@ -972,67 +1013,75 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
         slot = 0;
         ph ^= 1u;
       }
-      if (!mine) continue;
-      if (a.spill_off) add_spill<RT, NO>(a, s, lane, v.in + ((s + Nc <= nS) ? s + Nc : nS), acc);
-      RT qv[NO];
-      int qa[NO];
 #pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        RT q = act_ok ? acc[o].q(Rv[o], invN) : -(RT)INFINITY;
-        int ia = lane;
-        if constexpr (sizeof(RT) == 4) {
-          // order-preserving key (-0 keys like +0): the max in one redux,
-          // the lowest lane (= lowest action) among the maxima by ballot
-          const uint32_t bits = __float_as_uint((float)q + 0.0f);
-          const uint32_t key = bits ^ ((uint32_t)((int32_t)bits >> 31) | 0x80000000u);
-          const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
-          ia = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
-          q = __shfl_sync(0xffffffffu, q, ia);
-        } else {
+      for (int i = 0; i < kWsPer; ++i) {
+        if (warp + kWsCons * i >= rdesc.y) continue;
+        const int s = rdesc.x + warp + kWsCons * i;
+        Acc<RT> (&acc)[NO] = accs[i];
+        RT (&Rv)[NO] = Rvs[i];
+        const Pk old = olds_i[i];
+        const int wc = wcs[i];
+        if (a.spill_off) add_spill<RT, NO>(a, s, lane, v.in + ((s + Nc <= nS) ? s + Nc : nS), acc);
+        RT qv[NO];
+        int qa[NO];
 #pragma unroll
-          for (int m = 1; m < 32; m <<= 1) {
-            const RT oq = __shfl_xor_sync(0xffffffffu, q, m);
-            const int oa = __shfl_xor_sync(0xffffffffu, ia, m);
-            if (oq > q || (oq == q && oa < ia)) {
-              q = oq;
-              ia = oa;
+        for (int o = 0; o < NO; ++o) {
+          RT q = act_ok ? acc[o].q(Rv[o], invN) : -(RT)INFINITY;
+          int ia = lane;
+          if constexpr (sizeof(RT) == 4) {
+            // order-preserving key (-0 keys like +0): the max in one redux,
+            // the lowest lane (= lowest action) among the maxima by ballot
+            const uint32_t bits = __float_as_uint((float)q + 0.0f);
+            const uint32_t key = bits ^ ((uint32_t)((int32_t)bits >> 31) | 0x80000000u);
+            const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+            ia = __ffs(__ballot_sync(0xffffffffu, key == kmax)) - 1;
+            q = __shfl_sync(0xffffffffu, q, ia);
+          } else {
+#pragma unroll
+            for (int m = 1; m < 32; m <<= 1) {
+              const RT oq = __shfl_xor_sync(0xffffffffu, q, m);
+              const int oa = __shfl_xor_sync(0xffffffffu, ia, m);
+              if (oq > q || (oq == q && oa < ia)) {
+                q = oq;
+                ia = oa;
+              }
             }
           }
+          qv[o] = q;
+          qa[o] = ia;
         }
-        qv[o] = q;
-        qa[o] = ia;
-      }
-      if (s < s_lo || s >= s_hi) continue;
-      const bool term = (wc >> 8) != CLS_FREE;
-      Pk nv;
+        if (s < s_lo || s >= s_hi) continue;
+        const bool term = (wc >> 8) != CLS_FREE;
+        Pk nv;
 #pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        const bool upd = (live >> o) & 1u;
-        nv.v[o] = upd ? qv[o] : old.v[o];
-        if (upd) {
-          if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv[o] - old.v[o]));
-          else rd[o] = fmax(rd[o], fabs(qv[o] - old.v[o]));
-        }
-      }
-#pragma unroll
-      for (int o = NO; o < Pk::W; ++o) nv.v[o] = (RT)0;
-      int myqa = qa[0];
-#pragma unroll
-      for (int o = 1; o < NO; ++o)
-        if (lane == o) myqa = qa[o];
-      if (mylive) mypol[s] = term ? (int16_t)-1 : (int16_t)myqa;
-      if (lane == 0) v.out[s] = nv;
-      if (chg_out) {
-        if (s >= t_end) {   // entered a later layer: publish the finished one
-          if (chg && lane == 0) chg_out[t_cur] = 1;
-          chg = false;
-          t_cur = s / Nc;
-          t_end = (t_cur + 1) * Nc;
+        for (int o = 0; o < NO; ++o) {
+          const bool upd = (live >> o) & 1u;
+          nv.v[o] = upd ? qv[o] : old.v[o];
+          if (upd) {
+            if constexpr (sizeof(RT) == 4) rf[o] = fmaxf(rf[o], fabsf(qv[o] - old.v[o]));
+            else rd[o] = fmax(rd[o], fabs(qv[o] - old.v[o]));
+          }
         }
 #pragma unroll
-        for (int o = 0; o < NO; ++o) {   // bitwise: -0 vs +0 counts as a change
-          if constexpr (sizeof(RT) == 4) chg |= __float_as_uint(nv.v[o]) != __float_as_uint(old.v[o]);
-          else chg |= __double_as_longlong(nv.v[o]) != __double_as_longlong(old.v[o]);
+        for (int o = NO; o < Pk::W; ++o) nv.v[o] = (RT)0;
+        int myqa = qa[0];
+#pragma unroll
+        for (int o = 1; o < NO; ++o)
+          if (lane == o) myqa = qa[o];
+        if (mylive) mypol[s] = term ? (int16_t)-1 : (int16_t)myqa;
+        if (lane == 0) v.out[s] = nv;
+        if (chg_out) {
+          if (s >= t_end) {   // entered a later layer: publish the finished one
+            if (chg && lane == 0) chg_out[t_cur] = 1;
+            chg = false;
+            t_cur = s / Nc;
+            t_end = (t_cur + 1) * Nc;
+          }
+#pragma unroll
+          for (int o = 0; o < NO; ++o) {   // bitwise: -0 vs +0 counts as a change
+            if constexpr (sizeof(RT) == 4) chg |= __float_as_uint(nv.v[o]) != __float_as_uint(old.v[o]);
+            else chg |= __double_as_longlong(nv.v[o]) != __double_as_longlong(old.v[o]);
+          }
         }
       }
     }
@@ -1321,7 +1370,7 @@ static cudaError_t pipe_config(const SolveArgs &a, int64_t slices, PipeRange *pr
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t b = (int64_t)num_sms() * per_sm;
-    const int64_t want = (slices + 2 * kWsCons - 1) / (2 * kWsCons);   // >= 2 rounds per CTA
+    const int64_t want = (slices + 2 * kWsRound - 1) / (2 * kWsRound);   // >= 2 rounds per CTA
     if (b > want) b = want;
     if (b < 1) b = 1;
     *blocks = (int)b;

@@ -70,6 +70,11 @@ struct Build3Args {
   uint16_t *sinkc;
   void *R;
   unsigned long long *cnt;
+  // warp-per-slice kernel (FP32 rank counting): table words per warp, the
+  // list of slices it leaves to the CTA kernel, and (CTA kernel) that list
+  int32_t cap3;
+  uint32_t *defer;
+  const uint32_t *defer_in;
 };
 
 template <typename RT>
@@ -139,7 +144,12 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
   __syncthreads();
   for (;;) {
     if (tid == 0) {
-      s_slice = (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+      if (a.defer_in) {   // the slices the warp kernel left (count CNT_DEFER_N)
+        const unsigned long long i = atomicAdd(&a.cnt[CNT_DEFER_WORK], 1ULL);
+        s_slice = i < a.cnt[CNT_DEFER_N] ? (long long)a.defer_in[i] : (long long)a.n_slices;
+      } else {
+        s_slice = (long long)atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+      }
       s_rank = 0;
       s_total = 0;
     }
@@ -521,6 +531,317 @@ __global__ void __launch_bounds__(256, sizeof(RT) == 4 ? 4 : 1) build3d_kernel(B
   }
 }
 
+// ---- warp per slice (FP32 rank counting) ----
+// A warp builds one slice alone, in private shared memory and without block
+// barriers -- the 2-D warp kernel's scheme in three dimensions: pass 1 forms
+// u for the warp's (state, realization) items and reduces each state's exact
+// extremes per axis; the states' fine tables are laid out in the warp's table
+// memory; pass 2 forms u again and counts each realization at its fine
+// coordinate; an in-place 3-D prefix sum; then lane l emits row l exactly as
+// the CTA kernel's rank path does (the same offsets, eight-corner box sums,
+// entry order and R accumulation), so a slice's output does not depend on
+// the kernel that built it.  Slices whose tables do not fit the warp's memory
+// (or whose velocity extremes are not finite or widely spread) go to a list
+// that the CTA kernel builds afterwards.
+constexpr int kWarps3 = 8;   // warps per CTA of the warp kernel
+constexpr int kCap3 = 2048;  // table words per warp (8 KB)
+
+struct Warp3Acc {
+  unsigned long long tot = 0, dom = 0, samp = 0, maxw = 0;
+};
+
+// u of realization w of state s (layer t, cell c): the CTA kernel's phase A
+__device__ __forceinline__ void velocity3(const Build3Args &a, int64_t s, int64_t t, int64_t c, int w, float (&u)[3]) {
+  const float *vbar = static_cast<const float *>(a.vbar);
+  const float *modes = static_cast<const float *>(a.modes);
+  const float *yw = static_cast<const float *>(a.Y) + ((size_t)t * a.N + w) * a.K;
+  float vx = vbar[3 * s], vy = vbar[3 * s + 1], vz = vbar[3 * s + 2];
+  for (int k = 0; k < a.K; ++k) {
+    const float *ph = modes + 3 * ((t * a.K + k) * a.Nc + c);
+    vx = fmaf(yw[k], ph[0], vx);
+    vy = fmaf(yw[k], ph[1], vy);
+    vz = fmaf(yw[k], ph[2], vz);
+  }
+  u[0] = fmaf(vx, a.lam, 0.5f);
+  u[1] = fmaf(vy, a.lam, 0.5f);
+  u[2] = fmaf(vz, a.lam, 0.5f);
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+    if (!(fabsf(u[x]) < 1e30f)) u[x] = 1e30f;
+}
+
+__device__ __forceinline__ Geo3 shfl_geo3(const Geo3 &g, int src) {
+  Geo3 o;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    o.n0[x] = __shfl_sync(0xffffffffu, g.n0[x], src);
+    o.fmin[x] = __shfl_sync(0xffffffffu, g.fmin[x], src);
+    o.G[x] = __shfl_sync(0xffffffffu, g.G[x], src);
+  }
+  o.base = __shfl_sync(0xffffffffu, g.base, src);
+  return o;
+}
+
+// Slice sl by one warp; tab: the warp's cap words of table memory (zero).
+// Returns false when the slice was put on the CTA kernel's list.
+__device__ bool warp3_slice(const Build3Args &a, int64_t sl, uint32_t *tab, Warp3Acc &acc) {
+  const int lane = threadIdx.x & 31;
+  const int spw = a.spw, h = a.h, L = a.L;
+  const int64_t Nc = a.Nc, nxy = (int64_t)a.nx * a.ny;
+  const int q_l = lane / a.A_pad, a_l = lane % a.A_pad;
+  const bool act_ok = a_l < a.A;
+  const int q_t = lane % spw, wi = lane / spw, wstep = 32 / spw;
+  auto kind = [&](int64_t s) {
+    if (s >= a.nS) return (int)KIND_NONE;
+    if (a.target[s % Nc]) return (int)KIND_TERMINAL;
+    if (a.obstacle[s] || s / Nc == a.nt - 1) return (int)KIND_SINK;
+    return (int)KIND_SAMPLE;
+  };
+  const int64_t s_l = sl * spw + q_l, s_t = sl * spw + q_t;
+  const int kind_l = act_ok ? kind(s_l) : KIND_NONE;
+  const int kind_t = kind(s_t);
+  const int64_t t_t = s_t / Nc, c_t = s_t % Nc;
+  // ---- pass 1: exact extremes of u per state and axis
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (kind_t == KIND_SAMPLE) {
+    for (int w = wi; w < a.N; w += wstep) {
+      float u[3];
+      velocity3(a, s_t, t_t, c_t, w, u);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        mn[x] = fminf(mn[x], u[x]);
+        mx[x] = fmaxf(mx[x], u[x]);
+      }
+    }
+  }
+  for (int off = 16; off >= spw; off >>= 1) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      mn[x] = fminf(mn[x], __shfl_xor_sync(0xffffffffu, mn[x], off));
+      mx[x] = fmaxf(mx[x], __shfl_xor_sync(0xffffffffu, mx[x], off));
+    }
+  }
+  // lane q < spw: the fine table of state q (the CTA kernel's rules)
+  Geo3 g{};
+  long long cells = 0;
+  if (lane < spw && kind(sl * spw + lane) == KIND_SAMPLE) {
+    cells = 1;
+    for (int x = 0; x < 3 && cells > 0; ++x) {
+      if (!(mn[x] > -1e6f) || !(mx[x] < 1e6f) || mx[x] - mn[x] > 1024.f) {
+        cells = -1;
+        break;
+      }
+      const int S = a.act.D[x] + 1;
+      g.n0[x] = (int)floorf(mn[x]);
+      g.fmin[x] = fine3(mn[x], g.n0[x], S, a.act.T[x], a.act.D[x]);
+      g.G[x] = fine3(mx[x], g.n0[x], S, a.act.T[x], a.act.D[x]) - g.fmin[x] + 1;
+      cells *= (long long)(g.G[x] + 1);
+    }
+  }
+  long long total = 0;
+  bool fit = true;
+  for (int q = 0; q < spw; ++q) {
+    const long long cq = __shfl_sync(0xffffffffu, cells, q);
+    if (lane == q) g.base = (int)min(total, (long long)a.cap3);
+    if (cq < 0) fit = false;
+    total += max(cq, 0LL);
+  }
+  if (!fit || total > (long long)a.cap3) {   // the CTA kernel builds it
+    if (lane == 0) {
+      const unsigned long long i = atomicAdd(&a.cnt[CNT_DEFER_N], 1ULL);
+      a.defer[i] = (uint32_t)sl;
+    }
+    return false;
+  }
+  // ---- pass 2: one count per realization at its fine coordinate
+  const Geo3 gt = shfl_geo3(g, q_t);
+  if (kind_t == KIND_SAMPLE) {
+    const int Py = gt.G[1] + 1, Pz = gt.G[2] + 1;
+    const uint32_t hb = smem_u32(tab);
+#pragma unroll 1
+    for (int w = wi; w < a.N; w += wstep) {
+      float u[3];
+      velocity3(a, s_t, t_t, c_t, w, u);
+      int X = fine3(u[0], gt.n0[0], a.act.D[0] + 1, a.act.T[0], a.act.D[0]) - gt.fmin[0];
+      int Y = fine3(u[1], gt.n0[1], a.act.D[1] + 1, a.act.T[1], a.act.D[1]) - gt.fmin[1];
+      int Z = fine3(u[2], gt.n0[2], a.act.D[2] + 1, a.act.T[2], a.act.D[2]) - gt.fmin[2];
+      X = min(max(X, 0), gt.G[0] - 1);
+      Y = min(max(Y, 0), gt.G[1] - 1);
+      Z = min(max(Z, 0), gt.G[2] - 1);
+      const uint32_t idx = (uint32_t)(gt.base + ((X + 1) * Py + (Y + 1)) * Pz + (Z + 1));
+      asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + 4u * idx), "r"(1u));
+    }
+  }
+  __syncwarp();
+  // ---- in-place inclusive prefix sums along z, y and x (border planes stay zero)
+  for (int q = 0; q < spw; ++q) {
+    if (__shfl_sync(0xffffffffu, cells, q) <= 0) continue;
+    const Geo3 gq = shfl_geo3(g, q);
+    const int Gx = gq.G[0], Gy = gq.G[1], Gz = gq.G[2], Py = Gy + 1, Pz = Gz + 1;
+    uint32_t *P = tab + gq.base;
+    for (int ln = lane; ln < Gx * Gy; ln += 32) {
+      uint32_t *r = P + ((ln / Gy + 1) * Py + (ln % Gy + 1)) * Pz;
+      for (int z = 1; z <= Gz; ++z) r[z] += r[z - 1];
+    }
+    __syncwarp();
+    for (int ln = lane; ln < Gx * Gz; ln += 32) {
+      uint32_t *r = P + (ln / Gz + 1) * Py * Pz + (ln % Gz + 1);
+      for (int y = 1; y <= Gy; ++y) r[y * Pz] += r[(y - 1) * Pz];
+    }
+    __syncwarp();
+    for (int ln = lane; ln < Gy * Gz; ln += 32) {
+      uint32_t *r = P + (ln / Gz + 1) * Pz + (ln % Gz + 1);
+      for (int x = 1; x <= Gx; ++x) r[x * Py * Pz] += r[(x - 1) * Py * Pz];
+    }
+    __syncwarp();
+  }
+  // ---- emit: lane l = row (q_l, a_l), the CTA kernel's rank path
+  const Geo3 gl = shfl_geo3(g, q_l);
+  float umn[3], umx[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    umn[x] = __shfl_sync(0xffffffffu, mn[x], q_l);
+    umx[x] = __shfl_sync(0xffffffffu, mx[x], q_l);
+  }
+  auto rank_count = [&](int di, int dj, int dk) -> uint32_t {
+    const int off[3] = {di, dj, dk};
+    int c0[3], c1[3];
+    for (int x = 0; x < 3; ++x) {
+      const int S = a.act.D[x] + 1;
+      const int f0 = (off[x] - a.act.c[x][a_l] - gl.n0[x] - 1) * S + a.act.le[x][a_l] - gl.fmin[x];
+      c0[x] = max(f0, 0);
+      c1[x] = min(f0 + S - 1, gl.G[x] - 1);
+      if (c0[x] > c1[x]) return 0u;
+    }
+    const int Py = gl.G[1] + 1, Pz = gl.G[2] + 1;
+    const uint32_t *P = tab + gl.base;
+    auto at = [&](int x, int y, int z) { return P[(x * Py + y) * Pz + z]; };
+    const int x0 = c0[0], y0 = c0[1], z0 = c0[2], x1 = c1[0] + 1, y1 = c1[1] + 1, z1 = c1[2] + 1;
+    return at(x1, y1, z1) - at(x0, y1, z1) - at(x1, y0, z1) - at(x1, y1, z0) + at(x0, y0, z1) +
+           at(x0, y1, z0) + at(x1, y0, z0) - at(x0, y0, z0);
+  };
+  const int64_t ir = sl * 32 + lane;
+  const int64_t t = s_l / Nc, c = s_l % Nc;
+  const int64_t li = c % a.nx, lj = (c / a.nx) % a.ny, lk = c / nxy;
+  const int64_t nxt = (t + 1) * Nc;
+  int e = 0;
+  uint32_t sink = 0;
+  int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+  if (kind_l == KIND_SAMPLE) {
+    for (int x = 0; x < 3; ++x) {
+      lo[x] = box_offset(umn[x], a.act.c[x][a_l], a.act.th[x][a_l], h);
+      hi[x] = box_offset(umx[x], a.act.c[x][a_l], a.act.th[x][a_l], h);
+      if (lo[x] < -h || hi[x] > h) atomicAdd(&a.cnt[CNT_OVERFLOW], 1ULL);
+      lo[x] = max(lo[x], -h);
+      hi[x] = min(hi[x], h);
+    }
+    for (int dk = lo[2]; dk <= hi[2]; ++dk)
+      for (int dj = lo[1]; dj <= hi[1]; ++dj)
+        for (int di = lo[0]; di <= hi[0]; ++di) {
+          const uint32_t n = rank_count(di, dj, dk);
+          if (!n) continue;
+          const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
+          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+          if (!inside || a.obstacle[nxt + (kp * a.ny + jp) * a.nx + ip]) sink += n;
+          else ++e;
+        }
+  } else if (kind_l == KIND_SINK) {
+    sink = (uint32_t)a.N;
+  }
+  (void)L;
+  const bool cap_hit = e + (sink > 0 ? 1 : 0) > a.row_cap;
+  if (cap_hit) {
+    atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
+    e = 0;
+  }
+  int W = e;
+  for (int off = 16; off > 0; off >>= 1) W = max(W, __shfl_xor_sync(0xffffffffu, W, off));
+  unsigned long long base = 0;
+  if (lane == 0 && W > 0) base = atomicAdd(&a.cnt[CNT_POOL_COLS], (unsigned long long)W);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const bool fits = (W == 0) || (base + (unsigned long long)W <= a.pool_cap_cols);
+  if (!fits && lane == 0) atomicAdd(&a.cnt[CNT_POOL_FULL], 1ULL);
+  const bool write = fits && !cap_hit;
+  float Racc[3] = {0.f, 0.f, 0.f};
+  uint32_t *dst = a.pool + base * 32 + lane;
+  int k = 0;
+  if (kind_l == KIND_SAMPLE) {
+    const float F = a.act.F[a_l];
+    const float g_s = a.gbar ? static_cast<const float *>(a.gbar)[s_l] : 0.f;
+    for (int dk = lo[2]; dk <= hi[2]; ++dk)
+      for (int dj = lo[1]; dj <= hi[1]; ++dj)
+        for (int di = lo[0]; di <= hi[0]; ++di) {
+          const uint32_t n = rank_count(di, dj, dk);
+          if (!n) continue;
+          const int64_t ip = li + di, jp = lj + dj, kp = lk + dk;
+          const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny && kp >= 0 && kp < a.nz;
+          const int64_t cp = (kp * a.ny + jp) * a.nx + ip;
+          if (!inside || a.obstacle[nxt + cp]) continue;
+          if (write) dst[(size_t)k * 32] = entry_word((int)(dk * nxy + dj * a.nx + di), n);
+          ++k;
+          const bool is_t = a.target[cp] != 0;
+          const float g_sp = a.gbar ? static_cast<const float *>(a.gbar)[nxt + cp] : 0.f;
+          for (int o = 0; o < a.rw.n_obj; ++o)
+            Racc[o] = fmaf((float)n / (float)a.N, step_reward32(a.rw, a.rw.objs[o], F, g_s, g_sp, is_t), Racc[o]);
+        }
+    if (sink)
+      for (int o = 0; o < a.rw.n_obj; ++o) Racc[o] = fmaf((float)sink / (float)a.N, (float)a.rw.r_out, Racc[o]);
+  } else if (kind_l == KIND_SINK) {
+    for (int o = 0; o < a.rw.n_obj; ++o) Racc[o] = (float)a.rw.r_out;
+  }
+  if (!write) {
+    e = 0;
+    k = 0;
+  }
+  if (write)
+    for (int kk = k; kk < W; ++kk) dst[(size_t)kk * 32] = 0u;
+  if (!fits) sink = 0;
+  if (lane == 0) {
+    a.slice_off[sl] = (fits && W > 0) ? (uint32_t)base : kNoSlice;
+    a.slice_w[sl] = (fits && W > 0) ? (uint8_t)W : (uint8_t)0;
+  }
+  a.nnz[ir] = (uint8_t)e;
+  a.sinkc[ir] = (uint16_t)sink;
+  for (int o = 0; o < a.rw.n_obj; ++o) static_cast<float *>(a.R)[(int64_t)o * a.rows_pad + ir] = Racc[o];
+  int dom = e, tot = e + (sink > 0 ? 1 : 0);
+  for (int off = 16; off > 0; off >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    dom += __shfl_xor_sync(0xffffffffu, dom, off);
+  }
+  const int sampled = __popc(__ballot_sync(0xffffffffu, kind_l == KIND_SAMPLE));
+  acc.tot += (unsigned long long)tot;
+  acc.dom += (unsigned long long)dom;
+  acc.samp += (unsigned long long)sampled * (unsigned long long)a.N;
+  acc.maxw = max(acc.maxw, (unsigned long long)W);
+  __syncwarp();
+  for (int i = lane; i < (int)total; i += 32) tab[i] = 0u;   // zero for the next slice
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kWarps3, 2) build3d_warp_kernel(Build3Args a) {
+  extern __shared__ __align__(16) uint32_t smem3w[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *tab = smem3w + (size_t)warp * a.cap3;
+  for (int i = lane; i < a.cap3; i += 32) tab[i] = 0u;
+  __syncwarp();
+  Warp3Acc acc;
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+  for (;;) {
+    const int64_t sl = (int64_t)__shfl_sync(0xffffffffu, next, 0);
+    if (sl >= a.n_slices) break;
+    if (lane == 0) next = atomicAdd(&a.cnt[CNT_WORK], 1ULL);
+    warp3_slice(a, sl, tab, acc);
+  }
+  if (lane == 0) {
+    if (acc.tot) atomicAdd(&a.cnt[CNT_NNZ], acc.tot);
+    if (acc.dom) atomicAdd(&a.cnt[CNT_DOMAIN], acc.dom);
+    if (acc.samp) atomicAdd(&a.cnt[CNT_SAMPLES], acc.samp);
+    if (acc.maxw) atomicMax(&a.cnt[CNT_MAXROW], acc.maxw);
+  }
+}
+
 // FP32 landing-offset constants of one axis (same rule as the 2-D tables).
 static void axis_constants(const float *d, int A, int32_t *c, float *th) {
   for (int a = 0; a < A; ++a) {
@@ -729,14 +1050,44 @@ extern "C" mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *gri
     return fail(MDP_ERR_ARG);
   }
   const int64_t blocks = std::min<int64_t>((int64_t)num_sms() * per_sm, m->n_slices);
+  // FP32 rank counting: the warp-per-slice kernel first, the CTA kernel over
+  // the slices it leaves
+  const bool use_warp = prec == MDP_FP32 && ba.rank_ok;
+  uint32_t *defer = nullptr;
+  int64_t wblocks = 0;
+  size_t wsmem = 0;
+  if (use_warp) {
+    ba.cap3 = kCap3;
+    wsmem = (size_t)kWarps3 * kCap3 * 4;
+    TRY3(dev_alloc((void **)&defer, sizeof(uint32_t) * (size_t)m->n_slices, st));
+    ba.defer = defer;
+    TRY3(allow_max_smem((const void *)build3d_warp_kernel));
+    int wper = 0;
+    TRY3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, build3d_warp_kernel, 32 * kWarps3, wsmem));
+    if (wper < 1) {
+      release();
+      dev_free(defer, st);
+      set_error("the 3-D warp kernel's tables do not fit shared memory");
+      return fail(MDP_ERR_CUDA);
+    }
+    wblocks = std::min<int64_t>((int64_t)num_sms() * wper, (m->n_slices + kWarps3 - 1) / kWarps3);
+  }
   unsigned long long c[CNT_N];
   for (int attempt = 0;; ++attempt) {
     ba.pool = m->pool;
     ba.pool_cap_cols = cap_cols;
-    if (prec == MDP_FP64_CHECK)
+    if (prec == MDP_FP64_CHECK) {
       build3d_kernel<double><<<(unsigned)blocks, 256, smem, st>>>(ba);
-    else
+    } else if (use_warp) {
+      build3d_warp_kernel<<<(unsigned)wblocks, 32 * kWarps3, wsmem, st>>>(ba);
+      TRY3(cudaGetLastError());
+      Build3Args bd = ba;
+      bd.defer_in = defer;
+      build3d_kernel<float><<<(unsigned)blocks, 256, smem, st>>>(bd);
+      ++launches;
+    } else {
       build3d_kernel<float><<<(unsigned)blocks, 256, smem, st>>>(ba);
+    }
     TRY3(cudaGetLastError());
     ++launches;
     TRY3(cudaMemcpyAsync(c, m->cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -750,6 +1101,7 @@ extern "C" mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *gri
     TRY3(cudaMemsetAsync(m->cnt + CNT_WORK, 0, sizeof(unsigned long long) * (CNT_N - CNT_WORK), st));
   }
   release();
+  dev_free(defer, st);
   cudaEventRecord(ev1, st);
   cudaEventSynchronize(ev1);
   float ms = 0.f;

@@ -137,8 +137,8 @@ __device__ __forceinline__ int64_t spill_alloc(const BuildArgs &a, int64_t sl, i
 // accumulates R = sum_b (count_b/N) r_b + (count_sink/N) r_outbound in that
 // order, then allocates the slice's columns from the pool, writes them and
 // zeroes the staged words again.
-// Entries beyond row_cap go to the slice's spill block (HYB); a box of at
-// most row_cap bins cannot have any, otherwise a first pass counts them.
+// Every entry is staged (entry k in histogram row k); those beyond row_cap
+// then go to the slice's spill block (HYB).
 template <typename RT>
 __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, int64_t sl,
                            int kind, bool row_ok, int lo_x, int hi_x, int lo_y, int hi_y) {
@@ -154,24 +154,6 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, int64_t sl,
   lo_y = max(lo_y, -a.h);
   hi_x = min(hi_x, a.h);
   hi_y = min(hi_y, a.h);
-  int spill_n = 0;   // this row's in-domain successors beyond row_cap
-  if ((hi_x - lo_x + 1) * (hi_y - lo_y + 1) > a.row_cap && kind == KIND_SAMPLE && row_ok) {
-    const int64_t t = s / a.Nc, c = s % a.Nc;
-    const int i = (int)(c % a.nx), j = (int)(c / a.nx);
-    const int64_t nxt = (t + 1) * a.Nc;
-    int cnt = 0;
-    for (int dj = lo_y; dj <= hi_y; ++dj) {
-      const int jp = j + dj;
-      for (int di = lo_x; di <= hi_x; ++di) {
-        if (hist[(size_t)((dj + a.h) * a.L + a.h + di) * 32 + lane] == 0) continue;
-        const int ip = i + di;
-        const bool inside = ip >= 0 && ip < a.nx && jp >= 0 && jp < a.ny;
-        if (inside && !(a.cls[nxt + (int64_t)jp * a.nx + ip] & CLS_OBSTACLE)) ++cnt;
-      }
-    }
-    spill_n = max(cnt - a.row_cap, 0);
-  }
-  const int64_t sp_at = spill_alloc(a, sl, spill_n);
   if (kind == KIND_SINK) {
     sink = (uint32_t)a.N;
     for (int o = 0; o < a.rw.n_obj; ++o) {
@@ -205,9 +187,7 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, int64_t sl,
           sink += n;
           continue;
         }
-        const uint32_t wd = entry_word(dj * a.nx + di, n);
-        if (e < a.row_cap) hist[e * 32 + lane] = wd;
-        else if (sp_at >= 0) a.spill[sp_at + (e - a.row_cap)] = wd;
+        hist[e * 32 + lane] = entry_word(dj * a.nx + di, n);
         ++e;
         const bool is_t = (ccls & CLS_TARGET) != 0;
         RT g_sp = RT(0);
@@ -239,7 +219,11 @@ __device__ void emit_slice(const BuildArgs &a, uint32_t *hist, int64_t sl,
     }
   }
   int ell = min(e, a.row_cap);   // entries in the ELL columns
-  const int staged = ell;        // histogram words holding them
+  const int staged = e;          // histogram words holding the row's entries
+  // the rest of the row goes to the slice's spill block (HYB)
+  const int64_t sp_at = spill_alloc(a, sl, e - ell);
+  if (sp_at >= 0)
+    for (int k = ell; k < e; ++k) a.spill[sp_at + (k - ell)] = hist[k * 32 + lane];
 
   // slice width = widest row; allocate columns from the pool (bump allocator)
   int W = ell;

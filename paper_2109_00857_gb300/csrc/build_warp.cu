@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256, 3) build_warp_kernel(BuildArgs a) {
     // prefetch the next slice, unless this warp's share ends with this one
     const bool more = a.slices_per_warp == 0 || n < a.slices_per_warp;
     if (lane == 0) next = more ? atomicAdd(&a.cnt[CNT_WORK], 1ULL) : (unsigned long long)(a.slice_end - a.slice_begin);
-    warp_slice<KT, SPW>(a, sl, grid, tab, acc);
+    warp_slice<KT, SPW, true>(a, sl, grid, tab, acc);
     __syncwarp();
   }
   warp_flush(a, acc);

@@ -223,8 +223,11 @@ __device__ __forceinline__ void warp_flush(const BuildArgs &a, WarpAcc &acc) {
 // a.cap_bins words of fine-table memory, tab the model's rank tables
 // (kTab words, filled by load_rank_tables).
 // SPW > 0: states per warp fixed at compile time (1: A = 32, 2: A = 16);
-// SPW == 0: runtime spw.  KT: see kPhi.
-template <int KT, int SPW>
+// SPW == 0: runtime spw.  KT: see kPhi.  HYB: rows beyond row_cap keep
+// their tail in the slice's spill block; without it (the batched build, whose
+// models keep no spill area) such a row is counted in CNT_ROW_CAP and left
+// empty -- the lighter emit keeps the batched kernel free of register spills.
+template <int KT, int SPW, bool HYB>
 __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint32_t *grid, float *tab,
                                            WarpAcc &acc) {
   const int lane = threadIdx.x & 31;
@@ -437,8 +440,17 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   }
   // the first row_cap in-domain successors go to the ELL columns, the rest to
   // the slice's spill block (HYB)
+  bool cap_hit = false;
+  if constexpr (!HYB) {
+    cap_hit = e > a.row_cap;
+    if (cap_hit) {
+      atomicAdd(&a.cnt[CNT_ROW_CAP], 1ULL);
+      e = 0;
+    }
+  }
   int ell = min(e, a.row_cap);
-  const int64_t sp_at = spill_alloc(a, sl, e - ell);
+  int64_t sp_at = -1;
+  if constexpr (HYB) sp_at = spill_alloc(a, sl, e - ell);
   int W = ell;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) W = max(W, __shfl_xor_sync(0xffffffffu, W, off));
@@ -449,7 +461,7 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
   if (!fits && lane == 0) atomicAdd(&a.cnt[CNT_POOL_FULL], 1ULL);
   float Racc[3] = {0.f, 0.f, 0.f};
   uint32_t *dst = a.pool + base * 32 + lane;
-  const bool write = fits;
+  const bool write = fits && !cap_hit;
   int k = 0;
   if (kind_l == KIND_SAMPLE && active) {
     const float F = a.act.F[a_l];

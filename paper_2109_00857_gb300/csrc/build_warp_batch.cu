@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256, 3) build_warp_batch_kernel(const BuildArg
       __syncwarp();
       load_rank_tables(items[lo], tab);
     }
-    warp_slice<KT, SPW>(items[lo], g - prefix[lo], grid, tab, acc);
+    warp_slice<KT, SPW, false>(items[lo], g - prefix[lo], grid, tab, acc);
     __syncwarp();
   }
   if (cur >= 0) warp_flush(items[cur], acc);
