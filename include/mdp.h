@@ -301,14 +301,19 @@ mdp_status mdp_build3d(const mdp_env3d *env, const mdp_grid3d *grid, const mdp_a
                        int32_t N, int32_t subgrid_L, const int32_t *objs_h, int32_t n_obj,
                        void *stream, mdp_model *out);
 
-/* FP32 counting: a slice whose realizations fit one staging chunk (N <= 5461
- * for one state per slice), with at most 4 states per slice and at most 8
- * distinct step thresholds per axis, counts each realization once at its
- * fine coordinate (floor(u) - n0) S + rank(frac u) per axis and takes every
- * (action, offset bin) count as a box sum of the fine table's prefix sums;
- * other slices (and FP64_CHECK) count one increment per (realization,
- * action).  Both give the same model.  per_action = 1 forces the second way
- * for every slice (a reference for tests and comparisons). */
+/* FP32 counting, with at most 4 states per slice and at most 8 distinct step
+ * thresholds per axis: each realization is counted once at its fine
+ * coordinate (floor(u) - n0) S + rank(frac u) per axis, and every (action,
+ * offset bin) count is a box sum of the fine table's prefix sums -- by one
+ * warp per slice while the slice's tables fit the warp's 2048 words, else by
+ * a CTA per slice (whose realizations must fit one staging chunk: N <= 5461
+ * for one state per slice).  Other slices (and FP64_CHECK) count one
+ * increment per (realization, action).  All ways give the same model.
+ * per_action = 1 forces the last way for every slice (a reference for tests
+ * and comparisons).  3-D models keep every row in the sliced-ELL columns (no
+ * spill area): a row with more than 255 stored successors (possible for
+ * sub-grids above 5 x 5 x 5 cells) makes the build return
+ * MDP_ERR_ELL_OVERFLOW. */
 typedef struct {
   int32_t per_action;
 } mdp_build3d_opts;

@@ -1125,6 +1125,7 @@ extern "C" mdp_status mdp_build3d_ex(const mdp_env3d *env, const mdp_grid3d *gri
   m->nnz_domain = (int64_t)c[CNT_DOMAIN];
   m->max_row_nnz = (int32_t)c[CNT_MAXROW];
   m->samples = (int64_t)c[CNT_SAMPLES];
+  m->deferred = use_warp ? (int64_t)c[CNT_DEFER_N] : 0;   // slices the CTA kernel built
   {   // compaction into a pool of exactly the columns in use, in slice order
     uint32_t *np = nullptr;
     TRY3(dev_alloc((void **)&np, (size_t)std::max<uint64_t>(m->pool_cols, 1) * 128, st));

@@ -111,20 +111,29 @@ RANK_CASES = {
                                       amplitude=0.6, n_headings=5, elevations=(0.0, 0.7), speeds=(0.9,)),
     "spw4": lambda: inputs.make_env3d(nx=10, ny=7, nz=4, nt=3, K=3, N=150, L=7, sigma=(0.3, 0.2, 0.1), seed=6,
                                       amplitude=0.7, n_headings=3, elevations=(-0.5, 0.5), speeds=(1.0,)),
+    # wide velocity spreads: about half of the slices' fine tables exceed the
+    # warp kernel's memory and are built by the CTA kernel from its list
+    "mixed_kernels": lambda: inputs.make_env3d(nx=10, ny=9, nz=5, nt=3, K=3, N=300, L=11, sigma=(0.3, 0.25, 0.2),
+                                               seed=8, amplitude=0.3, n_headings=8, elevations=(-0.7, 0.0, 0.7),
+                                               speeds=(1.0,)),
 }
 
 
 @pytest.mark.parametrize("case", sorted(RANK_CASES))
 def test_rank_counting_equals_per_action_counting(mdp, case):
     """FP32: counting each realization once at its fine coordinates (box sums
-    of the prefix table) gives the same model as one increment per
-    (realization, action) -- counts, successors and R bit for bit."""
+    of the prefix table; the warp-per-slice kernel, and the CTA kernel for the
+    slices whose tables do not fit a warp) gives the same model as one
+    increment per (realization, action) -- counts, successors and R bit for
+    bit."""
     env = RANK_CASES[case]()
     objs = env.objectives if env.gbar is not None else (0,)
     d = mdp.DeviceEnv3D(env, mdp.MDP_FP32)
     fast = mdp.mdp_build3d(d, objs=objs)
     ref = mdp.mdp_build3d(d, objs=objs, per_action=True)
     assert fast.info().nnz == ref.info().nnz
+    if case == "mixed_kernels":   # both rank-counting kernels contributed
+        assert 0 < fast.info().wide_slices < env.nS
     for o in range(len(objs)):
         a = export_np(mdp, fast, o)
         b = export_np(mdp, ref, o)
