@@ -175,9 +175,15 @@ __device__ __forceinline__ void cta_run(const BuildArgs &a, uint32_t *smem, long
         run_mnx = fminf(run_mnx, cmnx); run_mxx = fmaxf(run_mxx, cmxx);
         run_mny = fminf(run_mny, cmny); run_mxy = fmaxf(run_mxy, cmxy);
         if (active) {
-          const int lox = land_offset(cmnx, cxl, thxl), hix = land_offset(cmxx, cxl, thxl);
-          const int loy = land_offset(cmny, cyl, thyl), hiy = land_offset(cmxy, cyl, thyl);
-          if (lox < -a.h || hix > a.h || loy < -a.h || hiy > a.h) active = false;
+          // far (or clamped non-finite) extremes leave the sub-grid; the
+          // integer landing offsets below are only formed for moderate ones
+          if (!(cmnx > -1e6f && cmxx < 1e6f && cmny > -1e6f && cmxy < 1e6f)) {
+            active = false;
+          } else {
+            const int lox = land_offset(cmnx, cxl, thxl), hix = land_offset(cmxx, cxl, thxl);
+            const int loy = land_offset(cmny, cyl, thyl), hiy = land_offset(cmxy, cyl, thyl);
+            if (lox < -a.h || hix > a.h || loy < -a.h || hiy > a.h) active = false;
+          }
         }
         // ---- phase B: count landings of this chunk
         if (active) {

@@ -55,7 +55,7 @@ __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
 template <int KT>
 constexpr int kPhi = KT > 0 ? KT : (KT < 0 ? -KT : kMaxModes);
 
-template <int KT>
+template <int KT, bool CLAMP = true>
 __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const float (&phx)[kPhi<KT>],
                                              const float (&phy)[kPhi<KT>], float vbx,
                                              float vby, int K, float lam) {
@@ -104,8 +104,10 @@ __device__ __forceinline__ float2 velocity_u(const float *__restrict__ yw, const
     }
   }
   float ux = fmaf(wx, lam, 0.5f), uy = fmaf(wy, lam, 0.5f);
-  if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
-  if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+  if constexpr (CLAMP) {
+    if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
+    if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+  }
   return make_float2(ux, uy);
 }
 
@@ -116,7 +118,7 @@ __device__ __forceinline__ void load_row4(const float *__restrict__ yw, float4 (
 #pragma unroll
   for (int v = 0; v < KT / 4; ++v) y[v] = __ldg(reinterpret_cast<const float4 *>(yw) + v);
 }
-template <int KT>
+template <int KT, bool CLAMP = true>
 __device__ __forceinline__ float2 velocity_row4(const float4 (&y)[KT / 4], const float (&phx)[kPhi<KT>],
                                                 const float (&phy)[kPhi<KT>], float vbx, float vby, float lam) {
   float wx = vbx, wy = vby;
@@ -129,8 +131,10 @@ __device__ __forceinline__ float2 velocity_row4(const float4 (&y)[KT / 4], const
     wx = fmaf(y[v].w, phx[k + 3], wx); wy = fmaf(y[v].w, phy[k + 3], wy);
   }
   float ux = fmaf(wx, lam, 0.5f), uy = fmaf(wy, lam, 0.5f);
-  if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
-  if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+  if constexpr (CLAMP) {
+    if (!(fabsf(ux) < 1e30f)) ux = 1e30f;
+    if (!(fabsf(uy) < 1e30f)) uy = 1e30f;
+  }
   return make_float2(ux, uy);
 }
 
@@ -305,7 +309,14 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     // sizes state q's fine table
     FineGeo g{};
     int cells = 0;
+    bool tame = true;
     if (kind_t == KIND_SAMPLE) {
+      // non-finite (clamped to 1e30) or far velocities: the CTA kernel's path
+      tame = mnx > -1e6f && mxx < 1e6f && mny > -1e6f && mxy < 1e6f;
+    }
+    if (kind_t == KIND_SAMPLE && !tame) {
+      cells = a.cap_bins + 1;
+    } else if (kind_t == KIND_SAMPLE) {
       g.n0x = (int)floorf(mnx);
       g.n0y = (int)floorf(mny);
       g.xmin = fine_coord(mnx, g.n0x, Sx, rx);
@@ -352,11 +363,11 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
     // ---- pass 2: one count per realization in its state's fine table
     if (kind_t == KIND_SAMPLE) {
       const uint32_t gbase = smem_u32(grid + gt.base);
+      // every u of the state is finite and within the extremes of pass 1 (the
+      // same floats): X in [0, gx), Y in [0, gy) with no clamping
       auto count = [&](float2 u) {
-        int X = fine_coord(u.x, gt.n0x, Sx, rx) - gt.xmin;
-        int Y = fine_coord(u.y, gt.n0y, Sy, ry) - gt.ymin;
-        X = min(max(X, 0), gt.gx - 1);
-        Y = min(max(Y, 0), gt.gy - 1);
+        const int X = fine_coord(u.x, gt.n0x, Sx, rx) - gt.xmin;
+        const int Y = fine_coord(u.y, gt.n0y, Sy, ry) - gt.ymin;
         red_add_shared(gbase + 4u * (uint32_t)((X + 1) * gt.pitch + Y + 1), 1u);
       };
       if constexpr (KT > 0 && KT % 4 == 0) {
@@ -370,11 +381,11 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
 #pragma unroll
           for (int v = 0; v < KT / 4; ++v) yc[v] = yn[v];
           if (w + wstep < N) load_row4<KT>(Yt + (size_t)(w + wstep) * K, yn);
-          count(velocity_row4<KT>(yc, phx, phy, vbx, vby, lam));
+          count(velocity_row4<KT, false>(yc, phx, phy, vbx, vby, lam));
         }
       } else {
 #pragma unroll 1
-        for (int w = wi; w < N; w += wstep) count(velocity_u<KT>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam));
+        for (int w = wi; w < N; w += wstep) count(velocity_u<KT, false>(Yt + (size_t)w * K, phx, phy, vbx, vby, K, lam));
       }
     }
     __syncwarp();

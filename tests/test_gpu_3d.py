@@ -111,11 +111,12 @@ RANK_CASES = {
                                       amplitude=0.6, n_headings=5, elevations=(0.0, 0.7), speeds=(0.9,)),
     "spw4": lambda: inputs.make_env3d(nx=10, ny=7, nz=4, nt=3, K=3, N=150, L=7, sigma=(0.3, 0.2, 0.1), seed=6,
                                       amplitude=0.7, n_headings=3, elevations=(-0.5, 0.5), speeds=(1.0,)),
-    # wide velocity spreads: about half of the slices' fine tables exceed the
-    # warp kernel's memory and are built by the CTA kernel from its list
-    "mixed_kernels": lambda: inputs.make_env3d(nx=10, ny=9, nz=5, nt=3, K=3, N=300, L=11, sigma=(0.3, 0.25, 0.2),
-                                               seed=8, amplitude=0.3, n_headings=8, elevations=(-0.7, 0.0, 0.7),
-                                               speeds=(1.0,)),
+    # wide velocity spreads and many step thresholds (20 actions: up to 8 per
+    # axis): about 30 % of the slices' fine tables exceed the warp kernel's
+    # memory and are built by the CTA kernel from its list
+    "mixed_kernels": lambda: inputs.make_env3d(nx=10, ny=9, nz=5, nt=3, K=3, N=300, L=11, sigma=(0.4, 0.3, 0.25),
+                                               seed=8, amplitude=0.2, n_headings=5,
+                                               elevations=(-0.7, -0.3, 0.3, 0.7), speeds=(1.0,)),
 }
 
 

@@ -150,6 +150,21 @@ def test_subgrid_overflow_is_an_error_on_both_paths(mdp):
         mdp.mdp_build(mdp.DeviceEnv(env, prec))
 
 
+def test_non_finite_velocities_are_a_subgrid_overflow(mdp):
+    """An infinite or NaN mean velocity in one cell lands outside every
+    sub-grid: the FP32 build reports MDP_ERR_SUBGRID_OVERFLOW (the warp kernel
+    hands such a state to the full-window kernel, which counts it), and the
+    same fields without it build."""
+    for bad in (np.inf, -np.inf, np.nan):
+        vbar = np.zeros((3, 7, 7, 2))
+        vbar[0, 3, 2, 1] = bad
+        env = custom_env(nx=7, ny=7, nt=3, N=8, L=5, vbar=vbar)
+        with pytest.raises(mdp.MdpError) as ei:
+            mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32))
+        assert ei.value.code == -3, bad
+    mdp.mdp_build(mdp.DeviceEnv(custom_env(nx=7, ny=7, nt=3, N=8, L=5), mdp.MDP_FP32))
+
+
 def test_automatic_subgrid_holds_every_landing(mdp):
     env = inputs.energy(nx=20, ny=20, nt=4, N=60)
     m = mdp.mdp_build(mdp.DeviceEnv(env, mdp.MDP_FP32), subgrid_L=0, objs=(0,))
