@@ -432,8 +432,11 @@ void mdp_batch_free(mdp_batch b);
  * ends with MDP_ERR_BUDGET if that exceeds the whole budget), so the requests
  * in flight never hold more than the budget.
  * Scheduling: a request runs on a stream whose priority follows its age among
- * the requests in flight (the oldest highest), so the GPU serves them close to
- * first come, first served while later ones fill the gaps. */
+ * the requests in flight (the oldest highest).  The oldest request uses the
+ * fastest (persistent) kernels; a younger one whose work (states x N) is at
+ * most a quarter of the oldest one's runs beside it with kernels that leave
+ * the SMs all along their run, filling the gaps; a larger one waits until it
+ * is the oldest.  Idle workers are woken most recently idle first. */
 typedef struct mdp_server_t *mdp_server;
 
 typedef struct {

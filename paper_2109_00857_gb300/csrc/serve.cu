@@ -75,6 +75,7 @@ struct Job {
   uint64_t pool_cols = 0;        // entry-pool size the charge covers
   uint64_t spill_words = 0;      // spill-area size the charge covers (rows beyond the row cap)
   int level = 0;                 // stream priority level (0 = highest)
+  double work = 0;               // realizations to count: states x N
   mdp_status status = MDP_ERR_PENDING;
   std::string error;
   int32_t sweeps = 0;
@@ -99,6 +100,7 @@ struct mdp_server_t {
   // is woken for nothing
   std::vector<std::unique_ptr<std::condition_variable>> wcv;
   std::vector<int> idle;
+  std::condition_variable cv_front;   // a request left the running list
   std::deque<std::shared_ptr<Job>> queue;
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   std::vector<std::unique_ptr<EnvEntry>> envs;
@@ -193,6 +195,9 @@ __global__ void target_block_kernel(uint8_t *tgt, int nx, int ny, int i0, int j0
 
 // slices per build warp when requests share the GPU (BuildArgs::slices_per_warp)
 constexpr int kServeSlicesPerWarp = 8;
+// a younger request runs beside the oldest one only when its work is at most
+// this fraction of the oldest one's
+constexpr double kServeShareFraction = 0.25;
 
 // Returns true when the request must be charged again for a larger pool or
 // for a spill area (job.pool_cols / job.spill_words then hold the exact need;
@@ -233,6 +238,16 @@ bool run_job(mdp_server_t *S, Job &job, cudaStream_t st, uint8_t *tgt) {
   // their run -- the build's warps take a few slices each and the sweeps use
   // small CTAs -- so the stream priorities (older first) decide whose blocks
   // run next: the younger request fills the SMs the older one leaves idle.
+  // A request far larger than the oldest one in flight would only slow that
+  // one down (each build needs the whole GPU): it waits until it is the
+  // oldest and then takes the persistent kernels.
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv_front.wait(lk, [&] {
+      return S->running.empty() || S->running.front().get() == &job ||
+             job.work <= kServeShareFraction * S->running.front()->work;
+    });
+  }
   auto younger = [&] {
     std::lock_guard<std::mutex> lk(S->mu);
     return !S->running.empty() && S->running.front().get() != &job;
@@ -388,6 +403,7 @@ void worker_main(mdp_server_t *S, int id) {
           S->running.erase(it);
           break;
         }
+      S->cv_front.notify_all();
       if (again) {
         const double cps = (double)job->pool_cols / (double)req_shape(e, job->req).n_slices;
         S->envs[job->req.env_id]->cols_per_slice = std::max(S->envs[job->req.env_id]->cols_per_slice, 1.1 * cps);
@@ -534,6 +550,7 @@ extern "C" mdp_status mdp_serve_submit(mdp_server S, const mdp_request *req, uin
   }
   auto job = std::make_shared<Job>();
   job->req = *req;
+  job->work = (double)req_shape(e, *req).nS * (double)req->N;
   job->pool_cols = pool_worst(e, *req);
   job->bytes = charge_bytes(e, *req, job->pool_cols, 0);
   if (job->bytes > (int64_t)S->budget) {   // too much for the budget: the widths seen so far
