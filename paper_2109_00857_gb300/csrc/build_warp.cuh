@@ -372,10 +372,11 @@ __device__ __forceinline__ void warp_slice(const BuildArgs &a, int64_t sl, uint3
       };
       if constexpr (KT > 0 && KT % 4 == 0) {
         // the next realization's coefficient row is loaded while this one
-        // is counted (its L2 latency overlaps the rank lookups)
+        // is counted (its L2 latency overlaps the rank lookups); two trips
+        // per loop iteration (measured: 127 ms against 131 ms unrolled once)
         float4 yn[KT / 4];
         if (wi < N) load_row4<KT>(Yt + (size_t)wi * K, yn);
-#pragma unroll 1
+#pragma unroll 2
         for (int w = wi; w < N; w += wstep) {
           float4 yc[KT / 4];
 #pragma unroll
