@@ -570,6 +570,29 @@ __device__ __forceinline__ void velocity3(const Build3Args &a, int64_t s, int64_
     if (!(fabsf(u[x]) < 1e30f)) u[x] = 1e30f;
 }
 
+// the same with the state's mode vectors in registers (K <= 4)
+__device__ __forceinline__ void velocity3r(const Build3Args &a, int64_t s, int64_t t, int w, const float (&ph)[4][3],
+                                           float (&u)[3]) {
+  const float *vbar = static_cast<const float *>(a.vbar);
+  const float *yw = static_cast<const float *>(a.Y) + ((size_t)t * a.N + w) * a.K;
+  float vx = vbar[3 * s], vy = vbar[3 * s + 1], vz = vbar[3 * s + 2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k < a.K) {
+      const float y = yw[k];
+      vx = fmaf(y, ph[k][0], vx);
+      vy = fmaf(y, ph[k][1], vy);
+      vz = fmaf(y, ph[k][2], vz);
+    }
+  }
+  u[0] = fmaf(vx, a.lam, 0.5f);
+  u[1] = fmaf(vy, a.lam, 0.5f);
+  u[2] = fmaf(vz, a.lam, 0.5f);
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+    if (!(fabsf(u[x]) < 1e30f)) u[x] = 1e30f;
+}
+
 __device__ __forceinline__ Geo3 shfl_geo3(const Geo3 &g, int src) {
   Geo3 o;
 #pragma unroll
@@ -601,12 +624,23 @@ __device__ bool warp3_slice(const Build3Args &a, int64_t sl, uint32_t *tab, Warp
   const int kind_l = act_ok ? kind(s_l) : KIND_NONE;
   const int kind_t = kind(s_t);
   const int64_t t_t = s_t / Nc, c_t = s_t % Nc;
+  // up to four modes: the state's mode vectors in registers for both passes
+  // (else each realization reloads them, 3K floats, from L1)
+  const bool preph = a.K <= 4;
+  float ph[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+      ph[k][x] = (preph && k < a.K && kind_t == KIND_SAMPLE)
+                     ? static_cast<const float *>(a.modes)[3 * ((t_t * a.K + k) * Nc + c_t) + x] : 0.f;
   // ---- pass 1: exact extremes of u per state and axis
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   if (kind_t == KIND_SAMPLE) {
     for (int w = wi; w < a.N; w += wstep) {
       float u[3];
-      velocity3(a, s_t, t_t, c_t, w, u);
+      if (preph) velocity3r(a, s_t, t_t, w, ph, u);
+      else velocity3(a, s_t, t_t, c_t, w, u);
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         mn[x] = fminf(mn[x], u[x]);
@@ -661,7 +695,8 @@ __device__ bool warp3_slice(const Build3Args &a, int64_t sl, uint32_t *tab, Warp
 #pragma unroll 1
     for (int w = wi; w < a.N; w += wstep) {
       float u[3];
-      velocity3(a, s_t, t_t, c_t, w, u);
+      if (preph) velocity3r(a, s_t, t_t, w, ph, u);
+      else velocity3(a, s_t, t_t, c_t, w, u);
       int X = fine3(u[0], gt.n0[0], a.act.D[0] + 1, a.act.T[0], a.act.D[0]) - gt.fmin[0];
       int Y = fine3(u[1], gt.n0[1], a.act.D[1] + 1, a.act.T[1], a.act.D[1]) - gt.fmin[1];
       int Z = fine3(u[2], gt.n0[2], a.act.D[2] + 1, a.act.T[2], a.act.D[2]) - gt.fmin[2];
