@@ -4,15 +4,19 @@
 //
 // Bellman backup (Sec. II-B): Q(s,a) = R(s,a) + sum_j P_j V(s'_j),
 // V_{k+1}(s) = max_a Q(s,a), pi(s) = argmax_a Q(s,a) (lowest index wins ties).
-// The slices' entry columns are copied into shared-memory stages by TMA bulk
-// copies and the successors' values V(s') gathered from the next time layer.
-// Two kernels with the same results bit for bit: warp per slice (lane l sums
-// row l; a redux.sync key or a segmented butterfly over the A_pad lanes of a
-// state gives the max and argmax), and for one state per slice the grouped
-// sweep (four states per warp step, each lane summing four rows and keeping a
-// running max, a 3-step shuffle per state).  Residual max|V_{k+1} - V_k| is
-// reduced on the device; a sweep whose predecessor met the tolerance exits at
-// once, so a fixed launch sequence needs no host round trip between sweeps.
+// The slices' entry columns reach shared memory by TMA bulk copies and the
+// successors' values V(s') are gathered from the next time layer.  Three
+// sweeps with the same results bit for bit: the warp-specialized sweep for
+// one state per slice (a producer warp copies rounds of slices into three
+// slots, 31 consumer warps each sum one slice, lane l row l, and take the max
+// and argmax with one redux.sync key per objective); warp per slice for
+// several states per slice (a segmented butterfly over the A_pad lanes of a
+// state); and the grouped sweep, kept for the batch's one-state-per-slice
+// class (four states per warp step, each lane summing four rows and keeping
+// a running max, a 3-step shuffle per state).  Residual max|V_{k+1} - V_k|
+// is reduced on the device; a sweep whose predecessor met the tolerance
+// exits at once, so a fixed launch sequence needs no host round trip between
+// sweeps.
 #include <algorithm>
 #include <cfloat>
 

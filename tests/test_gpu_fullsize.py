@@ -135,7 +135,7 @@ def test_four_layer_cut_solves_match_the_oracle_on_identical_P_R(mdp, large):
     es = cut(large, T_CUT, 4)
     objs = es.objectives
     model = mdp.mdp_build(mdp.DeviceEnv(es, mdp.MDP_FP32), objs=objs)
-    assert model.info().max_row_nnz <= 13   # the grouped sweep, as on the full model
+    assert model.info().max_row_nnz <= 13   # rows as narrow as on the full model
     Vs, ps, sts = mdp.mdp_solve_multi(model, tuple(range(3)), method=mdp.MDP_SOLVE_JACOBI, tol=0.0)
     Vl, pl, stl = mdp.mdp_solve_multi(model, tuple(range(3)), method=mdp.MDP_SOLVE_LAYERED)
     fx = oracle.fixed_mask(es)
