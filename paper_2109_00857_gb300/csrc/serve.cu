@@ -6,7 +6,7 @@
 // a scale for the coefficient standard deviations, a seed, N, an objective and
 // a tolerance.  Requests wait in a FIFO queue; max_slots worker threads, each
 // with its own CUDA stream, take the head of the queue as soon as a slot is
-// free and the request's device-memory estimate fits the HBM budget, then build
+// free and the request's device-memory charge fits the HBM budget, then build
 // and solve it: mdp_build over the remaining horizon t = start_t..nt-1, then
 // mdp_solve -- the layered pass for an exact request (tol = 0), Jacobi sweeps
 // to tol otherwise (from the request's starting values V0_h when given).
@@ -29,7 +29,15 @@
 // Scheduling: requests run on CUDA streams of graded priority by admission
 // order -- the oldest request in flight on the highest priority -- so the GPU
 // serves them close to first come, first served while later requests fill
-// the gaps the earlier ones leave (host round trips, short launches).
+// the gaps the earlier ones leave (host round trips, short launches).  The
+// oldest request in flight runs the persistent kernels (a build and sweeps
+// that occupy every SM); a younger request runs beside it only when its work
+// (states x N) is at most kServeShareFraction of the oldest one's, with
+// kernels that leave the SMs along their run (build warps that take
+// kServeSlicesPerWarp slices each, sweeps of small CTAs); a larger one waits
+// until it is the oldest, since two full-GPU builds would only slow the older
+// one down.  Idle workers wait on their own condition variables and a new
+// request wakes the most recently idle one, whose stream and buffers are warm.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
