@@ -778,10 +778,45 @@ __host__ __device__ constexpr size_t ws_old_bytes() { return (kWsSlots * kWsTab 
 template <typename RT>
 __host__ __device__ constexpr int ws_r_bytes(int n_obj) { return n_obj * kWsTab * 32 * (int)sizeof(RT); }
 
+// Work of the slices [lo, x) of a slice-ordered pool, in entry columns: their
+// columns plus kWsSliceWork per slice (a slice's own cost -- its R rows, its
+// state's values, the max over the actions -- weighed in columns).
+constexpr int64_t kWsSliceWork = 24;
+
+// CTA b of G takes the slices [ws_cut(b), ws_cut(b + 1)) of [lo, hi): the cut
+// is the first x whose work from lo reaches b/G of the whole, so every CTA
+// gets the same work however the widths vary (a pool in slice order has
+// slice_off = the prefix sums of the widths: the work is monotone in x).  A
+// 32-ary search over slice_off, about five dependent loads.  One warp calls it
+// with its lanes converged; every lane returns the cut.
+__device__ int64_t ws_cut(const SolveArgs &a, int64_t lo, int64_t hi, int64_t b, int64_t G) {
+  if (b <= 0) return lo;
+  if (b >= G) return hi;
+  const int lane = threadIdx.x & 31;
+  const uint32_t c0 = __ldg(a.slice_off + lo);
+  const int64_t c_end = (int64_t)__ldg(a.slice_off + hi - 1) + (int64_t)__ldg(a.slice_w + hi - 1);
+  const int64_t total = (c_end - (int64_t)c0) + kWsSliceWork * (hi - lo);
+  const int64_t tgt = total * b / G;   // < total: the cut lies in (lo, hi) or is hi
+  if (tgt <= 0) return lo;
+  // invariant: work(l) < tgt <= work(h)
+  int64_t l = lo, h = hi;
+  while (h - l > 1) {
+    const int64_t step = (h - l + 31) / 32;   // probes l + step, l + 2 step, ... below h
+    const int64_t x = l + (int64_t)(lane + 1) * step;
+    bool below = false;
+    if (x < h) below = (int64_t)(__ldg(a.slice_off + x) - c0) + kWsSliceWork * (x - lo) < tgt;
+    const int c = __popc(__ballot_sync(0xffffffffu, below));   // a prefix of the lanes
+    const int64_t nh = min(h, l + (int64_t)(c + 1) * step);
+    l += (int64_t)c * step;
+    h = nh;
+  }
+  return h;
+}
+
 template <typename RT, int NO>
-__device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<RT, NO> &v, int k, int64_t b_lo,
-                                                int64_t b_hi, const PipeRange &pr, unsigned char *sm,
-                                                double *wmax, int *s_flag) {
+__device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<RT, NO> &v, int k,
+                                                const PipeRange &pr, unsigned char *sm, double *wmax, int *s_flag,
+                                                int64_t *s_cut) {
   using Pk = VPack<RT, NO>;
   unsigned live = (1u << NO) - 1u;
   if (k > 1) {
@@ -793,9 +828,21 @@ __device__ __forceinline__ void bellman_body_ws(const SolveArgs &a, const VSet<R
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // one read of the error word for the whole CTA (an earlier launch timed out)
   if (tid == 0) *s_flag = *(volatile int *)a.err;
+  // this CTA's slices: equal work (slice-ordered pool) or equal counts
+  if (warp < 2) {
+    int64_t x;
+    if (a.pool_ordered && pr.sl_hi > pr.sl_lo) {
+      x = ws_cut(a, pr.sl_lo, pr.sl_hi, (int64_t)blockIdx.x + warp, gridDim.x);
+    } else {
+      const int64_t per_cta = (pr.sl_hi - pr.sl_lo + gridDim.x - 1) / gridDim.x;
+      x = min(pr.sl_hi, pr.sl_lo + ((int64_t)blockIdx.x + warp) * per_cta);
+    }
+    if (lane == 0) s_cut[warp] = x;
+  }
   __syncthreads();
   if (*s_flag) return;
   if (a.work && k >= 1 && blockIdx.x == 0 && tid == 0) a.work[k - 1] = (unsigned long long)(pr.sl_hi - pr.sl_lo);
+  const int64_t b_lo = s_cut[0], b_hi = s_cut[1];
   if (b_hi <= b_lo) return;
 
   WsHdr *hdr = reinterpret_cast<WsHdr *>(sm);
@@ -1114,12 +1161,9 @@ __global__ void __launch_bounds__(32 * (kWsCons + 1), 1) bellman_kernel_ws(Solve
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double wmax[kWsCons * NO];
   __shared__ int s_flag;
+  __shared__ int64_t s_cut[2];
   if (a.lflags && k >= 1 && !active_range(a, k, pr, blockIdx.x == 0)) return;
-  const int64_t total = pr.sl_hi - pr.sl_lo;
-  const int64_t per_cta = (total + gridDim.x - 1) / gridDim.x;
-  const int64_t b_lo = pr.sl_lo + (int64_t)blockIdx.x * per_cta;
-  const int64_t b_hi = min(pr.sl_hi, b_lo + per_cta);
-  bellman_body_ws<RT, NO>(a, v, k, b_lo, b_hi, pr, sm, wmax, &s_flag);
+  bellman_body_ws<RT, NO>(a, v, k, pr, sm, wmax, &s_flag, s_cut);
 }
 
 // Plan of batched Jacobi sweep k (one block): per model, the slices of the
